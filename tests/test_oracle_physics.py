@@ -120,6 +120,25 @@ def test_poiseuille_half_way_bounce_back(lam3):
 
 
 @pytest.mark.parametrize("alpha", [4 / 9, 0.95])
+def test_poiseuille_exact_with_tuned_ghost_rate(alpha):
+    """With half-way bounce-back, a two-rate collision reproduces the Poiseuille
+    parabola exactly when (1/lambda_even - 1/2)(1/lambda_odd - 1/2) = 3/16
+    (Ginzburg's "magic" combination).  Here lambda_3 plays the even (stress)
+    rate and Dellar's lambda_7 (J_x, J_y; App. A) the odd one: the discrete
+    steady state must then equal f/(2 eta) s (H - s) to round-off.  This pins
+    the force source (n = 1), the force-adjusted velocity u = (sum f c + G/2)/rho
+    (m = 1/2, Eq. equ_constants), nu(lambda_3) and the bounce-back geometry."""
+    ny, g, lam3 = 16, 1e-5, 0.7
+    lam7 = 1.0 / (3.0 / 16.0 / (1.0 / lam3 - 0.5) + 0.5)
+    p = _single_phase(4, ny, alpha, lam3, lambda7=lam7, g_acc=(g, 0.0), wall_y=True)
+    ref = A.poiseuille(ny, g, A.nu_of_lambda3(lam3))
+    R, B = O.init_state(np.ones((ny, 4)), np.broadcast_to(ref[:, None], (ny, 4)), np.zeros((ny, 4)), p)
+    R, B = O.run(R, B, p, 2000)
+    ux = O.fields(R, B, p)["ux"][:, 0]
+    assert np.abs(ux - ref).max() / ref.max() < 1e-10
+
+
+@pytest.mark.parametrize("alpha", [4 / 9, 0.95])
 def test_sound_damping_of_printed_scheme(alpha):
     """Effect of the isotropic (1/3) rho div u term of Eqs. equ_T_identity and
     Correction, implemented as printed.  A Chapman-Enskog expansion of the
