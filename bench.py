@@ -1,0 +1,317 @@
+"""Throughput of the fused two-colour D2Q9 chromodynamic MRT step on GB300.
+
+Workload: 8192 x 8192 periodic lattice, 64 seeded drops (radii uniform in
+[8, 64]), Lambda = 10, sigma = 0.005, beta = 0.67, nu = 1/6 (both fluids).
+One step = one lattice update of every node (all rows of the hot path, one
+fused kernel launch).  The state (2 x 4.8 GB of FP32 populations) is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cmrt|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (weak scaling, no collective on the data path); the
+time is the maximum over ranks.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead, on a bounded crop of the same workload.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "2-colour D2Q9 MRT MLUPS, % HBM roofline; low-prec/batched/adjoint vs plain FP32"
+UNIT = "MLUPS"
+BYTES_PER_CELL = 144  # 18 FP32 populations read + 18 written per node update
+N_SIDE = 8192
+WORKLOAD = "drops_8192x8192_periodic_64drops_Lambda10"
+KERNEL_SOURCES = ["paper_2005_04642_gb300/csrc/cmrt_step.cu", "paper_2005_04642_gb300/csrc/cmrt_device.cuh",
+                  "paper_2005_04642_gb300/csrc/cmrt_internal.h"]
+
+
+def workload_config():
+    return {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "ndrops": 64, "radii": [8, 64], "seed": 3,
+            "Lambda": 10.0, "sigma": 0.005, "beta": 0.67, "nu": 1.0 / 6.0, "storage": "fp32",
+            "l2": "no flush: state 9.7 GB (two 4.8 GB population buffers) >> 129 MB L2"}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(cells):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    scaled to `cells`, if the summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return float(d["dram_bytes_per_cell"]) * cells
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxs.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+def oracle_rate(side, steps, warmup):
+    """MLUPS of the FP64 NumPy oracle on a side x side crop of the workload,
+    run in a child process with BLAS pinned to one thread."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import cmrt_oracle as O
+from paper_2005_04642_gb300 import inputs as I
+d, rn, u = I.drops_8192()
+s = {side}
+d = dict(d, nx=s, ny=s)
+p = O.Params(**d)
+R, B = O.init_state(np.ascontiguousarray(rn[:s, :s]), u[0][:s, :s], u[1][:s, :s], p)
+R, B = O.run(R, B, p, {warmup})
+t0 = time.perf_counter()
+R, B = O.run(R, B, p, {steps})
+dt = time.perf_counter() - t0
+print(json.dumps({{"mlups": s * s * {steps} / dt / 1e6, "seconds": dt}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def crop_side(steps, warmup, budget_cell_updates=2.0e7):
+    side = int((budget_cell_updates / max(1, steps + warmup)) ** 0.5)
+    return max(64, min(1024, side - side % 8))
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    side = crop_side(args.steps, args.warmup)
+    r = oracle_rate(side, args.steps, args.warmup)
+    sample = (f"{side}x{side} crop of the {N_SIDE}^2 drops field, {args.warmup} untimed + {args.steps} timed "
+              f"FP64 NumPy oracle steps per run")
+    line = {"impl": "reference", "metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * r["seconds"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": r["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": r["mlups"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_cmrt(args, rank, world, local_rank):
+    import torch
+
+    from paper_2005_04642_gb300 import cmrt as cm
+    from paper_2005_04642_gb300 import inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    d, rn, u = I.drops_8192()
+    cells = d["nx"] * d["ny"]
+    rn32 = np.ascontiguousarray(rn, dtype=np.float32)
+    u32 = np.ascontiguousarray(u, dtype=np.float32)
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident throughput
+    lat = cm.Lattice(d, torch.from_numpy(rn32).cuda(), torch.from_numpy(u32).cuda(), stream=stream)
+    lat.step(args.warmup)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_launch0 = lat.launches
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    launches = lat.launches - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    diag = lat.diagnostics()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    per_launch_s = (ms / args.steps) * 1e-3
+
+    # ---- end to end through the C ABI with pinned host buffers
+    h_rn = torch.from_numpy(rn32).pin_memory()
+    h_u = torch.from_numpy(u32).pin_memory()
+    h_out = [torch.empty((d["ny"], d["nx"]), dtype=torch.float32).pin_memory() for _ in range(5)]
+    barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pr = cm.make_params(d)
+    ctx = cm.cmrt_init(pr, h_rn.data_ptr(), h_u.data_ptr(), stream.cuda_stream)
+    cm.cmrt_step(ctx, args.steps)
+    cm.cmrt_fields(ctx, *(o.data_ptr() for o in h_out))
+    e1.record(stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    cm.cmrt_destroy(ctx)
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * args.steps / float(te.item()) / 1e6
+    h2d = (h_rn.numel() + h_u.numel()) * 4
+    d2h = sum(o.numel() for o in h_out) * 4
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = BYTES_PER_CELL * cells / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "traffic": recorded_traffic(cells),
+                "algorithmic_bytes_per_launch": BYTES_PER_CELL * cells, "kernel": "k_chain<Step>",
+                "source_sha": kernel_source_sha()}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        side = crop_side(10, 2)
+        r = oracle_rate(side, 10, 2)
+        cpu = {"value": r["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{side}x{side} crop of the same drops field, 2 untimed + 10 timed FP64 NumPy oracle steps"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(), "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps,
+                    "what": "cmrt_init from pinned host rho^N_0, u_0 + K steps + cmrt_fields into pinned host buffers"},
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "check": {"mass_r": diag["mass_r"], "mass_b": diag["mass_b"], "nonfinite": diag["nonfinite"]}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="cmrt", choices=["cmrt", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_cmrt(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

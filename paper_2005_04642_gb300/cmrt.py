@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libcmrt (include/cmrt.h).
+
+Argument marshalling only: every step of the lattice update runs in the CUDA
+library.  Functions keep the C names; :class:`Lattice` is a convenience
+wrapper that takes PyTorch CUDA tensors or NumPy arrays.  If the library has
+not been built, loading fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcmrt.so")
+
+CMRT_OK, CMRT_EINVAL, CMRT_ENOMEM, CMRT_ECUDA, CMRT_ENONFINITE, CMRT_ESTATE, CMRT_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "CMRT_OK", 1: "CMRT_EINVAL", 2: "CMRT_ENOMEM", 3: "CMRT_ECUDA", 4: "CMRT_ENONFINITE",
+                5: "CMRT_ESTATE", 6: "CMRT_ETIMEOUT"}
+
+
+class cmrt_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("wall_y", ctypes.c_int32),
+        ("rho0_r", ctypes.c_double), ("rho0_b", ctypes.c_double),
+        ("alpha_r", ctypes.c_double), ("alpha_b", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
+        ("lambda3_r", ctypes.c_double), ("lambda3_b", ctypes.c_double),
+        ("lambda6", ctypes.c_double), ("lambda7", ctypes.c_double),
+        ("g_acc", ctypes.c_double * 2), ("g_vol", ctypes.c_double * 2),
+        ("visc_mode", ctypes.c_int32), ("eta", ctypes.c_double),
+        ("stencil_order", ctypes.c_int32), ("curvature_mode", ctypes.c_int32),
+        ("fixed_K", ctypes.c_double), ("ghost_N_mode", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("diag_every", ctypes.c_int32),
+    ]
+
+
+# (name, restype, argtypes) of every exported symbol declared in include/cmrt.h
+_SIGNATURES = [
+    ("cmrt_abi_version", ctypes.c_int32, []),
+    ("cmrt_params_size", ctypes.c_size_t, []),
+    ("cmrt_params_default", ctypes.c_int, [ctypes.POINTER(cmrt_params), ctypes.c_int32, ctypes.c_int32]),
+    ("cmrt_validate", ctypes.c_int, [ctypes.POINTER(cmrt_params)]),
+    ("cmrt_init", ctypes.c_int, [ctypes.POINTER(cmrt_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+    ("cmrt_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("cmrt_fields", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
+    ("cmrt_diagnostics", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("cmrt_get_populations", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("cmrt_set_populations", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("cmrt_synchronize", ctypes.c_int, [ctypes.c_void_p]),
+    ("cmrt_time", ctypes.c_int64, [ctypes.c_void_p]),
+    ("cmrt_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("cmrt_device_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("cmrt_destroy", None, [ctypes.c_void_p]),
+    ("cmrt_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcmrt.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcmrt is not built ({path} missing): run __graft_entry__.build() "
+                           "or python paper_2005_04642_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class CmrtError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status, ctx=None):
+    if status != CMRT_OK:
+        msg = load().cmrt_last_error(ctx)
+        raise CmrtError(status, msg.decode() if msg else "")
+
+
+def make_params(d: dict) -> cmrt_params:
+    """cmrt_params from a plain dictionary (keys as in the C struct)."""
+    lib = load()
+    p = cmrt_params()
+    _check(lib.cmrt_params_default(ctypes.byref(p), int(d["nx"]), int(d["ny"])))
+    for k, v in d.items():
+        if k in ("g_acc", "g_vol"):
+            arr = getattr(p, k)
+            arr[0], arr[1] = float(v[0]), float(v[1])
+        elif k == "wall_y":
+            p.wall_y = int(bool(v))
+        elif k == "dtype":
+            continue
+        elif hasattr(p, k):
+            ftype = dict(cmrt_params._fields_)[k]
+            setattr(p, k, int(v) if ftype is ctypes.c_int32 else float(v))
+    return p
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def cmrt_abi_version():
+    return load().cmrt_abi_version()
+
+
+def cmrt_validate(params: cmrt_params):
+    return load().cmrt_validate(ctypes.byref(params))
+
+
+def cmrt_init(params: cmrt_params, rho_n0_ptr: int, u0_ptr: int, stream_ptr: int):
+    h = ctypes.c_void_p()
+    _check(load().cmrt_init(ctypes.byref(params), rho_n0_ptr or None, u0_ptr or None, stream_ptr or None,
+                            ctypes.byref(h)))
+    return h
+
+
+def cmrt_step(ctx, n: int):
+    _check(load().cmrt_step(ctx, int(n)), ctx)
+
+
+def cmrt_fields(ctx, rho_r=0, rho_b=0, ux=0, uy=0, p=0):
+    _check(load().cmrt_fields(ctx, rho_r or None, rho_b or None, ux or None, uy or None, p or None), ctx)
+
+
+def cmrt_diagnostics(ctx):
+    out = (ctypes.c_double * 6)()
+    st = load().cmrt_diagnostics(ctx, out)
+    vals = list(out)
+    _check(st, ctx)
+    return vals
+
+
+def cmrt_get_populations(ctx, dst_ptr: int):
+    _check(load().cmrt_get_populations(ctx, dst_ptr), ctx)
+
+
+def cmrt_set_populations(ctx, src_ptr: int):
+    _check(load().cmrt_set_populations(ctx, src_ptr), ctx)
+
+
+def cmrt_synchronize(ctx):
+    _check(load().cmrt_synchronize(ctx), ctx)
+
+
+def cmrt_time(ctx):
+    return load().cmrt_time(ctx)
+
+
+def cmrt_launch_count(ctx):
+    return load().cmrt_launch_count(ctx)
+
+
+def cmrt_device_bytes(ctx):
+    return load().cmrt_device_bytes(ctx)
+
+
+def cmrt_destroy(ctx):
+    load().cmrt_destroy(ctx)
+
+
+def cmrt_last_error(ctx=None):
+    msg = load().cmrt_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+# ---------------------------------------------------------------- convenience wrapper
+def _ptr(x):
+    """Raw pointer of a torch tensor or NumPy array (must be contiguous float32)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous() and str(x.dtype) == "torch.float32"
+        return x.data_ptr()
+    assert x.flags["C_CONTIGUOUS"] and x.dtype == np.float32
+    return x.ctypes.data
+
+
+class Lattice:
+    """A two-colour lattice owned by libcmrt.
+
+    ``params`` is a plain dictionary (see :mod:`paper_2005_04642_gb300.inputs`);
+    ``rho_n0`` (ny, nx) and ``u0`` (2, ny, nx) are float32 NumPy arrays or CUDA
+    tensors.  Work runs on ``stream`` (a torch.cuda.Stream, default: the current
+    stream of the current device)."""
+
+    def __init__(self, params: dict, rho_n0=None, u0=None, stream=None):
+        import torch
+        self.torch = torch
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self._p = make_params(params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        keep = []
+
+        def as_f32(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                a = a.to(torch.float32).contiguous()
+            else:
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            keep.append(a)
+            return a
+
+        rn = as_f32(rho_n0)
+        uu = as_f32(u0)
+        self.ctx = cmrt_init(self._p, _ptr(rn), _ptr(uu), self.stream.cuda_stream)
+        self._keep = keep  # device inputs must outlive the queued init kernel
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cmrt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        cmrt_step(self.ctx, n)
+
+    def fields(self):
+        """dict of (ny, nx) float32 CUDA tensors: rho_r, rho_b, ux, uy, p."""
+        t = self.torch
+        out = {k: t.empty((self.ny, self.nx), dtype=t.float32, device="cuda") for k in ("rho_r", "rho_b", "ux", "uy", "p")}
+        cmrt_fields(self.ctx, *(out[k].data_ptr() for k in ("rho_r", "rho_b", "ux", "uy", "p")))
+        return out
+
+    def fields_host(self):
+        """Same as :meth:`fields`, written straight into NumPy arrays."""
+        out = {k: np.empty((self.ny, self.nx), dtype=np.float32) for k in ("rho_r", "rho_b", "ux", "uy", "p")}
+        cmrt_fields(self.ctx, *(out[k].ctypes.data for k in ("rho_r", "rho_b", "ux", "uy", "p")))
+        return out
+
+    def diagnostics(self):
+        v = cmrt_diagnostics(self.ctx)
+        return {"mass_r": v[0], "mass_b": v[1], "mom_x": v[2], "mom_y": v[3], "umax": v[4], "nonfinite": v[5]}
+
+    def populations(self):
+        """(2, 9, ny, nx) float32 CUDA tensor of the pre-collision populations."""
+        t = self.torch
+        out = t.empty((2, 9, self.ny, self.nx), dtype=t.float32, device="cuda")
+        cmrt_get_populations(self.ctx, out.data_ptr())
+        return out
+
+    def set_populations(self, pops):
+        a = pops
+        if hasattr(a, "data_ptr"):
+            a = a.to(self.torch.float32).contiguous()
+        else:
+            a = np.ascontiguousarray(a, dtype=np.float32)
+        cmrt_set_populations(self.ctx, _ptr(a))
+        if hasattr(a, "data_ptr"):
+            self.synchronize()
+
+    def synchronize(self):
+        cmrt_synchronize(self.ctx)
+
+    @property
+    def time(self):
+        return cmrt_time(self.ctx)
+
+    @property
+    def launches(self):
+        return cmrt_launch_count(self.ctx)

@@ -1,0 +1,145 @@
+// Initialisation and state import/export kernels of libcmrt.
+//
+// The library stores the post-collision populations P_{t-1}; the state of
+// the paper at time t is the pre-collision f(t) = stream(P_{t-1})
+// (Eq. equ_evolution).  These kernels translate between the two, and build
+// the initial state from a colour field and a velocity field.
+#include "cmrt_device.cuh"
+
+namespace cmrt {
+namespace {
+
+__device__ __forceinline__ int wrapx(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// Equilibrium populations of colour `col` at node (x, y) from rho^N_0 and u_0
+// (Eqs. equ_equ, eq_phi; rho_R = rho0_R (1 + rho^N)/2, rho_B = rho0_B (1 - rho^N)/2
+// inverts Eq. equ_rhoN_def), evaluated in FP64 and rounded once.
+struct InitIn {
+    const float* rho_n0;
+    const float* u0;
+    double rho0_r, rho0_b, alpha_r, alpha_b;
+};
+
+__device__ double eq_colour(const InitIn& in, size_t node, int i, int col, size_t plane) {
+    const double rn = in.rho_n0 ? static_cast<double>(in.rho_n0[node]) : -1.0;
+    const double ux = in.u0 ? static_cast<double>(in.u0[node]) : 0.0;
+    const double uy = in.u0 ? static_cast<double>(in.u0[plane + node]) : 0.0;
+    const double rr = in.rho0_r * (1.0 + rn) * 0.5;
+    const double rb = in.rho0_b * (1.0 - rn) * 0.5;
+    const double rho = rr + rb;
+    double phi;
+    if (i == 0) {
+        phi = (in.alpha_r * rr + in.alpha_b * rb) / rho;
+    } else {
+        phi = 1.8 * static_cast<double>(lw(i)) * ((1.0 - in.alpha_r) * rr + (1.0 - in.alpha_b) * rb) / rho;
+    }
+    const double cu = lcx(i) * ux + lcy(i) * uy;
+    const double w = (i == 0) ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 36.0 : 1.0 / 9.0);
+    const double f0 = rho * phi + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
+    return (col == 0 ? rr : rb) / rho * f0;
+}
+
+__global__ void k_init(InitIn in, int nx, int ny, int walls, float* __restrict__ post) {
+    const size_t plane = static_cast<size_t>(nx) * ny;
+    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < plane;
+         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int y = static_cast<int>(n / nx);
+        const int x = static_cast<int>(n - static_cast<size_t>(y) * nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            // P_i(s) streams to s + c_i; beyond a wall it returns to s as link opp(i).
+            const int ty = y + lcy(i);
+            size_t src;
+            int li;
+            if (walls && (ty < 0 || ty >= ny)) {
+                src = n;
+                li = lopp(i);
+            } else {
+                const int yy = wrapx(ty, ny);
+                src = static_cast<size_t>(yy) * nx + wrapx(x + lcx(i), nx);
+                li = i;
+            }
+            post[i * plane + n] = static_cast<float>(eq_colour(in, src, li, 0, plane));
+            post[(9 + i) * plane + n] = static_cast<float>(eq_colour(in, src, li, 1, plane));
+        }
+    }
+}
+
+// pre_i(r) = P_i(r - c_i), or P_opp(i)(r) where r - c_i lies beyond a wall.
+__global__ void k_stream_out(const float* __restrict__ post, int nx, int ny, int walls, float* __restrict__ pre) {
+    const size_t plane = static_cast<size_t>(nx) * ny;
+    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < plane;
+         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int y = static_cast<int>(n / nx);
+        const int x = static_cast<int>(n - static_cast<size_t>(y) * nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sy = y - lcy(i);
+            for (int c = 0; c < 2; ++c) {
+                float v;
+                if (walls && (sy < 0 || sy >= ny)) {
+                    v = post[(c * 9 + lopp(i)) * plane + n];
+                } else {
+                    v = post[(c * 9 + i) * plane + static_cast<size_t>(wrapx(sy, ny)) * nx + wrapx(x - lcx(i), nx)];
+                }
+                pre[(c * 9 + i) * plane + n] = v;
+            }
+        }
+    }
+}
+
+// Inverse of k_stream_out: P_i(s) = pre_i(s + c_i), or pre_opp(i)(s) where
+// s + c_i lies beyond a wall.
+__global__ void k_unstream_in(const float* __restrict__ pre, int nx, int ny, int walls, float* __restrict__ post) {
+    const size_t plane = static_cast<size_t>(nx) * ny;
+    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < plane;
+         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int y = static_cast<int>(n / nx);
+        const int x = static_cast<int>(n - static_cast<size_t>(y) * nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ty = y + lcy(i);
+            for (int c = 0; c < 2; ++c) {
+                float v;
+                if (walls && (ty < 0 || ty >= ny)) {
+                    v = pre[(c * 9 + lopp(i)) * plane + n];
+                } else {
+                    v = pre[(c * 9 + i) * plane + static_cast<size_t>(wrapx(ty, ny)) * nx + wrapx(x + lcx(i), nx)];
+                }
+                post[(c * 9 + i) * plane + n] = v;
+            }
+        }
+    }
+}
+
+dim3 flat_grid(size_t n) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks == 0) blocks = 1;
+    return dim3(static_cast<unsigned>(blocks));
+}
+
+}  // namespace
+
+// rho0/alpha are passed through StepParams' sources in FP64 by the caller.
+cudaError_t launch_init_fp64(const float* rho_n0, const float* u0, int nx, int ny, int walls, double rho0_r,
+                             double rho0_b, double alpha_r, double alpha_b, float* post, cudaStream_t s) {
+    InitIn in{rho_n0, u0, rho0_r, rho0_b, alpha_r, alpha_b};
+    k_init<<<flat_grid(static_cast<size_t>(nx) * ny), 256, 0, s>>>(in, nx, ny, walls, post);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_out(const float* post, const StepParams& P, float* pre, cudaStream_t s) {
+    k_stream_out<<<flat_grid(static_cast<size_t>(P.nx) * P.ny), 256, 0, s>>>(post, P.nx, P.ny, P.wall_y, pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unstream_in(const float* pre, const StepParams& P, float* post, cudaStream_t s) {
+    k_unstream_in<<<flat_grid(static_cast<size_t>(P.nx) * P.ny), 256, 0, s>>>(pre, P.nx, P.ny, P.wall_y, post);
+    return cudaGetLastError();
+}
+
+}  // namespace cmrt

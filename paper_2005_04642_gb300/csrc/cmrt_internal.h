@@ -1,0 +1,79 @@
+// Internal interface between the C ABI (cmrt_api.cu) and the kernels
+// (cmrt_step.cu, cmrt_aux.cu) of libcmrt.  Not installed, not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace cmrt {
+
+// Parameters of one step in the form the kernels use: FP32 coefficients
+// derived once on the host (in FP64) from cmrt_params.
+struct StepParams {
+    int nx, ny, wall_y;
+    int visc_mode, curvature_mode, ghost_N_mode;
+    float inv_rho0_r, inv_rho0_b;  // colour index (Eq. equ_rhoN_def)
+    float alpha_r, alpha_b;        // rest weights phi_0 (Eq. eq_phi)
+    float kphi_r, kphi_b;          // 9/5 (1 - alpha_C): phi_i = w_i (kphi_r rho_R + kphi_b rho_B) / rho
+    float cs2_r, cs2_b;            // 3/5 (1 - alpha_C): pressure (App. A)
+    float phip_r, phip_b;          // Phi' = phip_r rho_R + phip_b rho_B (App. A)
+    float neq_r, neq_b;            // h^(6).f^(0) = neq_r rho_R + neq_b rho_B (App. A)
+    float half_sigma, beta;
+    float nu_r, nu_b, eta;         // viscosity model (Sec. 2)
+    float lambda6, lambda7;
+    float gacc_x, gacc_y, gvol_x, gvol_y;
+    float fixed_K;
+};
+
+// Output buffers of the field pass (any may be null).
+struct FieldOut {
+    float* rho_r;
+    float* rho_b;
+    float* ux;
+    float* uy;
+    float* p;
+};
+
+// Geometry of the fused row-marching kernel: a CTA of kThreads threads owns a
+// strip of kTileX columns (plus a 4-column halo on each side, kWin columns in
+// all) and marches down kRows rows of it.
+constexpr int kThreads = 128;
+constexpr int kWin = 128;
+constexpr int kHalo = 4;
+constexpr int kTileX = kWin - 2 * kHalo;  // 120
+constexpr int kRing = 8;                  // rows of post-collision populations kept in shared memory
+
+enum class Pass : int { Step = 0, Fields = 1, Diag = 2 };
+
+// Number of FP64 partial sums each CTA of the diagnostics pass writes.
+constexpr int kDiagSlots = 6;  // mass_r, mass_b, mom_x, mom_y, max|u|^2, non-finite count
+
+size_t chain_smem_bytes();
+// grid of the chain kernel for a lattice, with `rows` rows per CTA
+dim3 chain_grid(int nx, int ny, int rows);
+
+// One fused step: src holds the post-collision populations P_{t-1}
+// (float[18][ny][nx]), dst receives P_t.  flag is set non-zero if a node has a
+// non-finite density.
+cudaError_t launch_step(const float* src, float* dst, const StepParams& P, int rows,
+                        unsigned* flag, cudaStream_t s);
+// Fields of the state whose post-collision populations are in src.
+cudaError_t launch_fields(const float* src, const StepParams& P, int rows, FieldOut out,
+                          cudaStream_t s);
+// Per-CTA FP64 partial diagnostics into partials[grid][kDiagSlots].
+cudaError_t launch_diag_partials(const float* src, const StepParams& P, int rows,
+                                 double* partials, cudaStream_t s);
+// Reduces nblocks partial rows into out[kDiagSlots] (one CTA).
+cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s);
+
+// Initial state: writes into post the populations P_{-1} whose streaming gives
+// the equilibrium state of Eq. equ_equ at t = 0.
+cudaError_t launch_init_fp64(const float* rho_n0, const float* u0, int nx, int ny, int walls, double rho0_r,
+                             double rho0_b, double alpha_r, double alpha_b, float* post, cudaStream_t s);
+// Pre-collision populations f(t) = stream(P_{t-1}) into pre[18][ny][nx].
+cudaError_t launch_stream_out(const float* post, const StepParams& P, float* pre, cudaStream_t s);
+// Inverse: post P_{t-1} such that stream(P_{t-1}) = pre.
+cudaError_t launch_unstream_in(const float* pre, const StepParams& P, float* post, cudaStream_t s);
+
+}  // namespace cmrt

@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Same seeded inputs on both sides.  Population parity is element by element;
+field parity uses the norms of the parity bar: max |d rho_C| / max |rho_C| and
+max |d u| / max(max |u_ref|, 0.01), at most 1e-5 after 100 steps and 1e-3
+after 10k steps, colour-mass drift at most 1e-6.  Population tolerances for a
+few steps are 2e-6 of the largest population (FP32 storage is ~6e-8 relative;
+a few steps of FP32 arithmetic stay well inside).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import cmrt_oracle as O
+from paper_2005_04642_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2005_04642_gb300 import cmrt as cm  # noqa: E402
+
+cm.load()
+
+
+def _oracle_run(d, rn, u, n):
+    p = O.Params(**d)
+    R, B = O.init_state(rn, u[0], u[1], p)
+    R, B = O.run(R, B, p, n)
+    return p, R, B
+
+
+def _pop_err(lat, R, B):
+    got = lat.populations().double().cpu().numpy()
+    ref = np.stack([R, B])
+    return np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def _field_errs(lat, p, R, B):
+    g = {k: v.double().cpu().numpy() for k, v in lat.fields().items()}
+    f = O.fields(R, B, p)
+    out = {}
+    for k in ("rho_r", "rho_b", "p"):
+        out[k] = np.abs(g[k] - f[k]).max() / np.abs(f[k]).max()
+    uref = max(np.abs(np.stack([f["ux"], f["uy"]])).max(), 0.01)
+    for k in ("ux", "uy"):
+        out[k] = np.abs(g[k] - f[k]).max() / uref
+    return out
+
+
+# ---------------------------------------------------------------- initial state
+@pytest.mark.parametrize("wall", [False, True])
+def test_initial_populations_match(wall):
+    d, rn, u = I.static_drop(n=40, radius=10.0)
+    d["wall_y"] = wall
+    lat = cm.Lattice(d, rn, u)
+    p = O.Params(**d)
+    R, B = O.init_state(rn, u[0], u[1], p)
+    assert _pop_err(lat, R, B) < 2e-7
+    lat.close()
+
+
+# ---------------------------------------------------------------- one to a few steps, many shapes
+CASES = [
+    # (name, nx, ny, wall, extra params)
+    ("tiny4x4", 4, 4, False, {}),
+    ("odd5x3", 5, 3, False, {}),
+    ("odd7x5_walls", 7, 5, True, {}),
+    ("1x6", 1, 6, False, {}),
+    ("6x1", 6, 1, False, {}),
+    ("ragged250x300", 250, 300, False, {}),
+    ("walls130x140", 130, 140, True, {"g_acc": (2e-5, -1e-5)}),
+    ("visc_eta", 48, 40, True, {"visc_mode": 1, "eta": 0.2}),
+    ("fixedK_ghostN", 36, 44, False, {"curvature_mode": 1, "fixed_K": 0.05, "ghost_N_mode": 1}),
+    ("rates_force", 64, 24, False, {"lambda3_r": 1.6, "lambda3_b": 0.7, "lambda6": 1.3, "lambda7": 0.6,
+                                    "g_vol": (1e-5, 2e-5), "sigma": 0.02}),
+]
+
+
+@pytest.mark.parametrize("name,nx,ny,wall,extra", CASES, ids=[c[0] for c in CASES])
+def test_steps_match_oracle_elementwise(name, nx, ny, wall, extra):
+    rn, u = I.random_state_fields(nx, ny, seed=zlib.crc32(name.encode()) % 1000)
+    d = I.base_params(nx, ny, rho0_r=1.0, rho0_b=0.1, wall_y=wall, **extra)
+    nsteps = 3
+    p, R, B = _oracle_run(d, rn, u, nsteps)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(nsteps)
+    err = _pop_err(lat, R, B)
+    lat.close()
+    assert err < 2e-6, err
+
+
+def test_set_then_step_matches_oracle():
+    nx, ny = 96, 70
+    d = I.base_params(nx, ny, rho0_r=1.0, rho0_b=0.01, alpha_light=0.5)
+    rn, u = I.random_state_fields(nx, ny, seed=7, amplitude=0.02)
+    p = O.Params(**d)
+    R, B = O.init_state(rn, u[0], u[1], p)
+    rng = np.random.default_rng(1)
+    R = R * (1 + rng.uniform(-0.02, 0.02, R.shape))
+    B = B * (1 + rng.uniform(-0.02, 0.02, B.shape))
+    lat = cm.Lattice(d)
+    pops = np.stack([R, B]).astype(np.float32)
+    lat.set_populations(pops)
+    back = lat.populations().cpu().numpy()
+    assert np.array_equal(back, pops)  # import/export is exact
+    R32, B32 = pops[0].astype(np.float64), pops[1].astype(np.float64)
+    R1, B1 = O.run(R32, B32, p, 2)
+    lat.step(2)
+    assert _pop_err(lat, R1, B1) < 2e-6
+    lat.close()
+
+
+# ---------------------------------------------------------------- parity bar on the workloads
+def test_static_drop_100_steps_parity_bar():
+    d, rn, u = I.static_drop()
+    p, R, B = _oracle_run(d, rn, u, 100)
+    lat = cm.Lattice(d, rn, u)
+    d0 = lat.diagnostics()
+    lat.step(100)
+    errs = _field_errs(lat, p, R, B)
+    d1 = lat.diagnostics()
+    lat.close()
+    for k, v in errs.items():
+        assert v <= 1e-5, (k, v)
+    assert abs(d1["mass_r"] - d0["mass_r"]) / d0["mass_r"] <= 1e-6
+    assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 1e-6
+
+
+def test_layered_walls_100_steps_parity_bar():
+    d, rn, u = I.layered_channel(nx=16, ny=128, Lambda=100.0, visc_ratio=10.0, g=1e-6)
+    p, R, B = _oracle_run(d, rn, u, 100)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(100)
+    errs = _field_errs(lat, p, R, B)
+    lat.close()
+    for k, v in errs.items():
+        assert v <= 1e-5, (k, v)
+
+
+@pytest.mark.slow
+def test_static_drop_10k_steps_parity_bar():
+    d, rn, u = I.static_drop()
+    p, R, B = _oracle_run(d, rn, u, 10000)
+    lat = cm.Lattice(d, rn, u)
+    d0 = lat.diagnostics()
+    lat.step(10000)
+    errs = _field_errs(lat, p, R, B)
+    d1 = lat.diagnostics()
+    lat.close()
+    for k, v in errs.items():
+        assert v <= 1e-3, (k, v)
+    assert abs(d1["mass_r"] - d0["mass_r"]) / d0["mass_r"] <= 1e-6
+    assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 1e-6
+
+
+def test_diagnostics_match_oracle():
+    d, rn, u = I.static_drop(n=48, radius=12.0)
+    d["g_acc"] = (1e-5, -2e-5)
+    p, R, B = _oracle_run(d, rn, u, 20)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(20)
+    g = lat.diagnostics()
+    lat.close()
+    ref = O.diagnostics(R, B, p)
+    for k in ("mass_r", "mass_b"):
+        assert abs(g[k] - ref[k]) / ref[k] < 1e-6
+    for k in ("mom_x", "mom_y"):
+        assert abs(g[k] - ref[k]) < 1e-6 * ref["mass_r"]
+    assert abs(g["umax"] - ref["umax"]) < 1e-5 * max(ref["umax"], 0.01)
+    assert g["nonfinite"] == 0
+
+
+def test_fields_host_and_device_pointers_agree():
+    d, rn, u = I.static_drop(n=32, radius=8.0)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(7)
+    dev = {k: v.cpu().numpy() for k, v in lat.fields().items()}
+    host = lat.fields_host()
+    lat.close()
+    for k in dev:
+        assert np.array_equal(dev[k], host[k]), k
+
+
+def test_host_inputs_equal_device_inputs():
+    d, rn, u = I.static_drop(n=32, radius=8.0)
+    a = cm.Lattice(d, rn, u)
+    b = cm.Lattice(d, torch.tensor(rn, dtype=torch.float32, device="cuda"),
+                   torch.tensor(u, dtype=torch.float32, device="cuda"))
+    a.step(3)
+    b.step(3)
+    assert torch.equal(a.populations(), b.populations())
+    a.close()
+    b.close()
+
+
+# ---------------------------------------------------------------- failure handling (host-made)
+def test_nonfinite_state_is_reported_and_context_fails():
+    d, rn, u = I.static_drop(n=32, radius=8.0)
+    d["diag_every"] = 1
+    lat = cm.Lattice(d, rn, u)
+    pops = lat.populations().cpu().numpy()
+    pops[0, 0, 5, 5] = np.nan
+    lat.set_populations(pops)
+    with pytest.raises(cm.CmrtError) as ei:
+        lat.step(2)
+    assert ei.value.status == cm.CMRT_ENONFINITE
+    with pytest.raises(cm.CmrtError) as ei:
+        lat.step(1)
+    assert ei.value.status == cm.CMRT_ESTATE
+    lat.close()
+
+
+def test_zero_steps_is_a_noop_and_counts_launches():
+    d, rn, u = I.static_drop(n=32, radius=8.0)
+    lat = cm.Lattice(d, rn, u)
+    before = lat.populations()
+    n0 = lat.launches
+    lat.step(0)
+    assert lat.launches == n0 and lat.time == 0
+    assert torch.equal(before, lat.populations())
+    lat.step(4)
+    assert lat.time == 4
+    lat.close()
+
+
+# ---------------------------------------------------------------- full size, sampled
+def _window(arr, cy, cx, h):
+    ny, nx = arr.shape[-2:]
+    ys = (np.arange(cy - h, cy + h + 1)) % ny
+    xs = (np.arange(cx - h, cx + h + 1)) % nx
+    return arr[..., ys[:, None], xs[None, :]]
+
+
+def test_full_size_drops_workload_sampled_nodes():
+    """The 8192^2 periodic drops workload in the benchmark's launch
+    configuration: one step, checked at sampled nodes against the oracle
+    stepping a 13 x 13 window around each (a node depends on nothing beyond
+    radius 5 in one step), plus colour-mass conservation over 20 steps."""
+    d, rn, u = I.drops_8192()
+    lat = cm.Lattice(d, rn, u)
+    lat.step(3)
+    pre = lat.populations()
+    rng = np.random.default_rng(0)
+    # sample near interfaces and in the bulk
+    inter = np.argwhere(np.abs(rn) < 0.9)
+    picks = [tuple(inter[i]) for i in rng.choice(len(inter), 24, replace=False)]
+    picks += [tuple(x) for x in rng.integers(0, 8192, size=(8, 2))]
+    picks += [(0, 0), (8191, 8191), (0, 8191), (4095, 8190)]
+    h = 6
+    wins = []
+    for (y, x) in picks:
+        ys = torch.arange(y - h, y + h + 1, device="cuda") % 8192
+        xs = torch.arange(x - h, x + h + 1, device="cuda") % 8192
+        wins.append(pre[:, :, ys][:, :, :, xs].double().cpu().numpy())
+    m0 = lat.diagnostics()
+    lat.step(1)
+    post = lat.populations()
+    got = [post[:, :, y, x].double().cpu().numpy() for (y, x) in picks]
+    lat.step(19)
+    m1 = lat.diagnostics()
+    lat.close()
+    dw = dict(d, nx=2 * h + 1, ny=2 * h + 1)
+    pw = O.Params(**dw)
+    for w, g in zip(wins, got):
+        R1, B1 = O.step(w[0], w[1], pw)
+        ref = np.stack([R1[:, h, h], B1[:, h, h]])
+        assert np.abs(g - ref).max() <= 2e-6 * max(np.abs(ref).max(), 0.1)
+    assert abs(m1["mass_r"] - m0["mass_r"]) / m0["mass_r"] <= 1e-6
+    assert abs(m1["mass_b"] - m0["mass_b"]) / m0["mass_b"] <= 1e-6
