@@ -42,10 +42,19 @@ KERNEL_SOURCES = ["paper_2005_04642_gb300/csrc/cmrt_step.cu", "paper_2005_04642_
                   "paper_2005_04642_gb300/csrc/cmrt_internal.h"]
 
 
-def workload_config():
-    return {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "ndrops": 64, "radii": [8, 64], "seed": 3,
+def workload_config(side=N_SIDE):
+    ndrops = max(1, round(64 * (side / N_SIDE) ** 2))
+    name = WORKLOAD if side == N_SIDE else f"drops_{side}x{side}_periodic_{ndrops}drops_Lambda10"
+    return {"workload": name, "nx": side, "ny": side, "ndrops": ndrops, "radii": [8, 64], "seed": 3,
             "Lambda": 10.0, "sigma": 0.005, "beta": 0.67, "nu": 1.0 / 6.0, "storage": "fp32",
-            "l2": "no flush: state 9.7 GB (two 4.8 GB population buffers) >> 129 MB L2"}
+            "l2": f"no flush: state {2 * 72 * side * side / 1e9:.2f} GB (two population buffers) >> 129 MB L2"}
+
+
+def make_workload(side):
+    from paper_2005_04642_gb300 import inputs as I
+    if side == N_SIDE:
+        return I.drops_8192()
+    return I.random_drops(side, side, workload_config(side)["ndrops"], 8.0, 64.0, 3, Lambda=10.0)
 
 
 def kernel_source_sha():
@@ -207,7 +216,7 @@ def run_cmrt(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    d, rn, u = I.drops_8192()
+    d, rn, u = make_workload(args.side)
     cells = d["nx"] * d["ny"]
     rn32 = np.ascontiguousarray(rn, dtype=np.float32)
     u32 = np.ascontiguousarray(u, dtype=np.float32)
@@ -283,7 +292,7 @@ def run_cmrt(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(), "clocks": clk.summary(),
+            "config": workload_config(args.side), "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
                     "what": "cmrt_init from pinned host rho^N_0, u_0 + K steps + cmrt_fields into pinned host buffers"},
@@ -302,6 +311,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cmrt", choices=["cmrt", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=N_SIDE,
+                    help="lattice side; smaller sides (same drop density) are for profiling captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

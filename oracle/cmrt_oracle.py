@@ -147,9 +147,13 @@ class Params:
         return self.rho0_r / self.rho0_b
 
 
-# Normal guard: where |grad rho^N|^2 is below this, n-hat is taken as zero
-# (the paper's n-hat = -grad rho^N / |grad rho^N| is undefined there, Sec. 2).
-NORMAL_GUARD2 = 1e-24
+# Regularisation of the unit normal: n-hat = -grad rho^N / max(|grad rho^N|, eps).
+# The paper's n-hat = -grad rho^N / |grad rho^N| (Sec. 2) is undefined where the
+# gradient vanishes, e.g. at the centre of a symmetric drop, where rho_R rho_B /
+# rho need not be small: there the recolour direction would be set by round-off.
+# Reading: below eps the normal shrinks smoothly to zero (no segregation where
+# there is no interface); above eps it is the paper's unit vector.
+NORMAL_EPS = 1e-4
 
 
 # ---------------------------------------------------------------------------
@@ -269,11 +273,11 @@ def gradient(field_, p: Params, parity=1, order=2):
 
 
 def unit_normal(gx, gy, p: Params):
-    """n-hat = -grad rho^N / |grad rho^N| (Sec. 2), zero where |grad rho^N|^2 < 1e-24."""
+    """n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised as
+    -grad rho^N / max(|grad rho^N|, 1e-4) where the gradient vanishes."""
     dt = p.dtype
-    mag2 = gx * gx + gy * gy
-    ok = mag2 >= dt(NORMAL_GUARD2)
-    inv = np.where(ok, dt(1.0) / np.sqrt(np.where(ok, mag2, dt(1.0))), dt(0.0))
+    mag = np.sqrt(gx * gx + gy * gy)
+    inv = dt(1.0) / np.maximum(mag, dt(NORMAL_EPS))
     return -gx * inv, -gy * inv
 
 

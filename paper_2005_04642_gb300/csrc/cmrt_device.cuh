@@ -63,8 +63,10 @@ __device__ __forceinline__ float ddy(float n, float s, float ne, float nw, float
     return (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * ((ne - se) + (nw - sw));
 }
 
-// Guard of the unit normal: where |grad rho^N|^2 is below this the normal is
-// taken as zero (n-hat = -grad rho^N / |grad rho^N| is undefined there).
-constexpr float kNormalGuard2 = 1e-24f;
+// Regularisation of the unit normal, n-hat = -grad rho^N / max(|grad rho^N|, eps):
+// the paper's unit vector wherever an interface is resolved, shrinking smoothly
+// to zero where the colour gradient vanishes (there its direction would be
+// set by round-off).
+constexpr float kNormalEps = 1e-4f;
 
 }  // namespace cmrt

@@ -204,13 +204,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
                 float gx, gy;
                 grad_at([&](int r) { return R.A(r, 0); }, yb, t, gx, gy);
+                // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
                 const float mag2 = gx * gx + gy * gy;
-                float nhx = 0.f, nhy = 0.f;
-                if (mag2 >= kNormalGuard2) {
-                    const float inv = rsqrtf(mag2);
-                    nhx = -gx * inv;  // n-hat = -grad rho^N / |grad rho^N| (Sec. 2)
-                    nhy = -gy * inv;
-                }
+                const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+                const float nhx = -gx * inv;
+                const float nhy = -gy * inv;
                 R.B(yb, 0)[t] = gx;
                 R.B(yb, 1)[t] = gy;
                 R.B(yb, 2)[t] = nhx;
@@ -339,6 +337,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const float aB = rb * inv_rho;
                     const float phim = (P.kphi_r * rr + P.kphi_b * rb) * inv_rho;  // phi_i / w_i, i != 0
                     const float seg = P.beta * rr * rb * inv_rho * phim;
+                    const bool red_major = rr >= rb;
                     const size_t o = static_cast<size_t>(yd) * nx + gxo;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
@@ -350,8 +349,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                         const float fp = f[i] + df;  // f+ = f + M^{-1} dm
                         float d = 0.0f;
                         if (i != 0) d = seg * lw(i) * (chx(i) * ex + chy(i) * ey);
-                        dst[i * plane + o] = fmaf(aR, fp, d);
-                        dst[(9 + i) * plane + o] = fmaf(aB, fp, -d);
+                        // the minority colour directly, the majority as the rest of f+,
+                        // so that R++ + B++ = f+ holds to one rounding of the majority
+                        const float r_pp = fmaf(aR, fp, d);
+                        const float b_pp = fmaf(aB, fp, -d);
+                        dst[i * plane + o] = red_major ? fp - b_pp : r_pp;
+                        dst[(9 + i) * plane + o] = red_major ? b_pp : fp - r_pp;
                     }
                 } else if (MODE == Pass::Fields) {
                     const size_t o = static_cast<size_t>(yd) * nx + gxo;
