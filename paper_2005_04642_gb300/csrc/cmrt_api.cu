@@ -287,7 +287,12 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
         }
         c->dev_bytes += state_bytes;
     }
-    c->rows = 128;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    c->rows = cmrt::chain_rows(p->nx, p->ny, sms);
     const dim3 g = cmrt::chain_grid(p->nx, p->ny, c->rows);
     c->n_partials = static_cast<int>(g.x * g.y);
     if (cudaMalloc(&c->d_flag, sizeof(unsigned)) != cudaSuccess ||

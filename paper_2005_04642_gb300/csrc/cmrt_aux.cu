@@ -14,33 +14,18 @@ __device__ __forceinline__ int wrapx(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Equilibrium populations of colour `col` at node (x, y) from rho^N_0 and u_0
-// (Eqs. equ_equ, eq_phi; rho_R = rho0_R (1 + rho^N)/2, rho_B = rho0_B (1 - rho^N)/2
-// inverts Eq. equ_rhoN_def), evaluated in FP64 and rounded once.
+// Initial state (t = 0): at each node the equilibrium of Eq. equ_equ with
+// phi_i of Eq. eq_phi, split by colour as C_i = (rho_C / rho) f^(0)_i, from
+// rho_R = rho0_R (1 + rho^N_0)/2 and rho_B = rho0_B (1 - rho^N_0)/2 (which
+// inverts Eq. equ_rhoN_def).  Evaluated once per node in FP64 and rounded
+// once.  Each node writes its links to where the first step's pull streaming
+// will find them: f_i(r) goes to P_i(r - c_i), or to P_opp(i)(r) where
+// r - c_i lies beyond a wall (half-way bounce-back).
 struct InitIn {
     const float* rho_n0;
     const float* u0;
     double rho0_r, rho0_b, alpha_r, alpha_b;
 };
-
-__device__ double eq_colour(const InitIn& in, size_t node, int i, int col, size_t plane) {
-    const double rn = in.rho_n0 ? static_cast<double>(in.rho_n0[node]) : -1.0;
-    const double ux = in.u0 ? static_cast<double>(in.u0[node]) : 0.0;
-    const double uy = in.u0 ? static_cast<double>(in.u0[plane + node]) : 0.0;
-    const double rr = in.rho0_r * (1.0 + rn) * 0.5;
-    const double rb = in.rho0_b * (1.0 - rn) * 0.5;
-    const double rho = rr + rb;
-    double phi;
-    if (i == 0) {
-        phi = (in.alpha_r * rr + in.alpha_b * rb) / rho;
-    } else {
-        phi = 1.8 * static_cast<double>(lw(i)) * ((1.0 - in.alpha_r) * rr + (1.0 - in.alpha_b) * rb) / rho;
-    }
-    const double cu = lcx(i) * ux + lcy(i) * uy;
-    const double w = (i == 0) ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 36.0 : 1.0 / 9.0);
-    const double f0 = rho * phi + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
-    return (col == 0 ? rr : rb) / rho * f0;
-}
 
 __global__ void k_init(InitIn in, int nx, int ny, int walls, float* __restrict__ post) {
     const size_t plane = static_cast<size_t>(nx) * ny;
@@ -48,22 +33,35 @@ __global__ void k_init(InitIn in, int nx, int ny, int walls, float* __restrict__
          n += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const int y = static_cast<int>(n / nx);
         const int x = static_cast<int>(n - static_cast<size_t>(y) * nx);
+        const double rn = in.rho_n0 ? static_cast<double>(in.rho_n0[n]) : -1.0;
+        const double ux = in.u0 ? static_cast<double>(in.u0[n]) : 0.0;
+        const double uy = in.u0 ? static_cast<double>(in.u0[plane + n]) : 0.0;
+        const double rr = in.rho0_r * (1.0 + rn) * 0.5;
+        const double rb = in.rho0_b * (1.0 - rn) * 0.5;
+        const double rho = rr + rb;
+        const double inv_rho = 1.0 / rho;
+        const double ar = rr * inv_rho, ab = rb * inv_rho;
+        const double phi0 = (in.alpha_r * rr + in.alpha_b * rb) * inv_rho;
+        const double phim = 1.8 * ((1.0 - in.alpha_r) * rr + (1.0 - in.alpha_b) * rb) * inv_rho;
+        const double usq = ux * ux + uy * uy;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            // P_i(s) streams to s + c_i; beyond a wall it returns to s as link opp(i).
-            const int ty = y + lcy(i);
-            size_t src;
+            const double w = (i == 0) ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 36.0 : 1.0 / 9.0);
+            const double cu = lcx(i) * ux + lcy(i) * uy;
+            const double phi = (i == 0) ? phi0 : w * phim;
+            const double f0 = rho * phi + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            const int ty = y - lcy(i);
+            size_t dst;
             int li;
             if (walls && (ty < 0 || ty >= ny)) {
-                src = n;
+                dst = n;
                 li = lopp(i);
             } else {
-                const int yy = wrapx(ty, ny);
-                src = static_cast<size_t>(yy) * nx + wrapx(x + lcx(i), nx);
+                dst = static_cast<size_t>(wrapx(ty, ny)) * nx + wrapx(x - lcx(i), nx);
                 li = i;
             }
-            post[i * plane + n] = static_cast<float>(eq_colour(in, src, li, 0, plane));
-            post[(9 + i) * plane + n] = static_cast<float>(eq_colour(in, src, li, 1, plane));
+            post[li * plane + dst] = static_cast<float>(ar * f0);
+            post[(9 + li) * plane + dst] = static_cast<float>(ab * f0);
         }
     }
 }

@@ -52,6 +52,8 @@ constexpr int kDiagSlots = 6;  // mass_r, mass_b, mom_x, mom_y, max|u|^2, non-fi
 size_t chain_smem_bytes();
 // grid of the chain kernel for a lattice, with `rows` rows per CTA
 dim3 chain_grid(int nx, int ny, int rows);
+// rows per CTA chosen for a lattice on a device with `sms` multiprocessors
+int chain_rows(int nx, int ny, int sms);
 
 // One fused step: src holds the post-collision populations P_{t-1}
 // (float[18][ny][nx]), dst receives P_t.  flag is set non-zero if a node has a

@@ -24,7 +24,9 @@
 //
 // The collision is written in increment form, f+ = f + M^{-1} dm with
 // dm = Lambda (m^(0) - m) + S (App. A, Eq. 38 minus m): the increments are
-// small, so FP32 rounding stays at the level of population storage.
+// small, so FP32 rounding stays at the level of population storage.  The
+// reconstruction M^{-1} dm is grouped by the parity of each column k^(p)
+// under c -> -c, which the k vectors of App. A have by construction.
 #include "cmrt_device.cuh"
 
 namespace cmrt {
@@ -42,6 +44,21 @@ constexpr int kBFloats = 4 * kBF * kWin;
 constexpr int kCF = 4;
 constexpr int kCFloats = 4 * kCF * kWin;
 constexpr int kSmemFloats = kPopFloats + kAFloats + kBFloats + kCFloats;
+// 16-byte chunks of one ring row (18 planes x 128 columns) and chunks per thread
+constexpr int kChunksPerPlane = kWin / 4;
+constexpr int kRowChunks = kPlanes * kChunksPerPlane;
+constexpr int kChunkIters = (kRowChunks + kThreads - 1) / kThreads;
+
+// The reconstruction below relies on these symmetries of App. A's k vectors.
+static_assert(kinv(4, 3) == kinv(8, 3) && kinv(4, 4) == kinv(8, 4) && kinv(4, 6) == kinv(8, 6), "even x");
+static_assert(kinv(4, 1) == -kinv(8, 1) && kinv(4, 7) == -kinv(8, 7), "odd x");
+static_assert(kinv(6, 3) == kinv(2, 3) && kinv(6, 4) == kinv(2, 4) && kinv(6, 6) == kinv(2, 6), "even y");
+static_assert(kinv(6, 2) == -kinv(2, 2) && kinv(6, 8) == -kinv(2, 8), "odd y");
+static_assert(kinv(2, 3) == kinv(8, 4) && kinv(2, 4) == kinv(8, 3) && kinv(2, 2) == kinv(8, 1) &&
+              kinv(2, 8) == kinv(8, 7), "x <-> y");
+static_assert(kinv(1, 3) == kinv(1, 4) && kinv(1, 1) == kinv(1, 2) && kinv(1, 7) == kinv(1, 8), "diagonal");
+static_assert(kinv(8, 2) == 0.f && kinv(8, 5) == 0.f && kinv(8, 8) == 0.f && kinv(0, 1) == 0.f &&
+              kinv(0, 5) == 0.f && kinv(0, 7) == 0.f, "zeros");
 
 struct Rings {
     float* pop;
@@ -56,13 +73,11 @@ struct Rings {
     __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
 };
 
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ void cp_async16(unsigned smem_addr, const float* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ void cp_async4(unsigned smem_addr, const float* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -75,40 +90,61 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Issue the asynchronous copy of post-collision row `row` (unwrapped index)
-// of the window [x0 - 4, x0 + 124) into its ring slot.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+
+// Per-thread plan of the asynchronous row copies: which 16-byte chunks of a
+// ring row this thread fetches, as (shared offset, global offset) pairs that
+// are the same for every row of the strip.
 template <bool VEC>
-__device__ __forceinline__ void issue_row(const Rings& R, const float* __restrict__ src, int row, int x0,
-                                          int nx, int ny, size_t plane) {
-    const int gy = wrap(row, ny);
-    const float* base = src + static_cast<size_t>(gy) * nx;
-    if (VEC) {
-        constexpr int kChunks = kWin / 4;
-        for (int c = threadIdx.x; c < kPlanes * kChunks; c += kThreads) {
-            const int q = c / kChunks;
-            const int w4 = (c - q * kChunks) * 4;
-            const int gx = wrap(x0 - kHalo + w4, nx);
-            cp_async16(R.P(row, q) + w4, base + q * plane + gx);
-        }
-    } else {
-        for (int c = threadIdx.x; c < kPlanes * kWin; c += kThreads) {
-            const int q = c / kWin;
-            const int w = c - q * kWin;
-            const int gx = wrap(x0 - kHalo + w, nx);
-            cp_async4(R.P(row, q) + w, base + q * plane + gx);
+struct CopyPlan {
+    static constexpr int kN = VEC ? kChunkIters : kPlanes;
+    unsigned soff[kN];  // byte offset inside a ring row
+    size_t goff[kN];    // element offset inside a global row (plane * nx * ny + column)
+    int n;
+
+    __device__ __forceinline__ void init(int x0, int nx, size_t plane) {
+        n = 0;
+        if (VEC) {
+#pragma unroll
+            for (int m = 0; m < kN; ++m) {
+                const int c = threadIdx.x + m * kThreads;
+                const int q = c / kChunksPerPlane;
+                const int w4 = (c - q * kChunksPerPlane) * 4;
+                soff[m] = static_cast<unsigned>((q * kWin + w4) * sizeof(float));
+                goff[m] = static_cast<size_t>(q) * plane + wrap(x0 - kHalo + w4, nx);
+                if (c < kRowChunks) n = m + 1;
+            }
+        } else {
+            const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
+#pragma unroll
+            for (int q = 0; q < kN; ++q) {
+                soff[q] = static_cast<unsigned>((q * kWin + threadIdx.x) * sizeof(float));
+                goff[q] = static_cast<size_t>(q) * plane + gx;
+            }
+            n = kN;
         }
     }
-}
+
+    __device__ __forceinline__ void issue(unsigned ring_row_addr, const float* grow) const {
+#pragma unroll
+        for (int m = 0; m < kN; ++m) {
+            if (m < n) {
+                if (VEC) cp_async16(ring_row_addr + soff[m], grow + goff[m]);
+                else cp_async4(ring_row_addr + soff[m], grow + goff[m]);
+            }
+        }
+    }
+};
 
 // Pre-collision populations at (row y, window column t): pull from the
 // post-collision ring, f_i(r) = P_i(r - c_i) (Eq. equ_evolution), with
 // half-way bounce-back P_opp(i)(r) where r - c_i lies beyond a wall.
-__device__ __forceinline__ void gather(const Rings& R, int y, int t, bool walls, int ny, float (&fr)[9],
-                                       float (&fb)[9]) {
+template <bool WALLS>
+__device__ __forceinline__ void gather(const Rings& R, int y, int t, int ny, float (&fr)[9], float (&fb)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sy = y - lcy(i);
-        if (walls && (sy < 0 || sy >= ny)) {
+        if (WALLS && (sy < 0 || sy >= ny)) {
             fr[i] = R.P(y, lopp(i))[t];
             fb[i] = R.P(y, 9 + lopp(i))[t];
         } else {
@@ -118,26 +154,35 @@ __device__ __forceinline__ void gather(const Rings& R, int y, int t, bool walls,
     }
 }
 
-// Compact derivative of a ring field at (row y, column t).
+__device__ __forceinline__ float sum9(const float (&v)[9]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// Compact derivatives of a ring field around (row y, column t).
 template <typename Row>
-__device__ __forceinline__ void grad_at(Row rowp, int y, int t, float& gx, float& gy) {
+__device__ __forceinline__ float ddx_at(Row rowp, int y, int t) {
     const float* n = rowp(y + 1);
     const float* m = rowp(y);
     const float* s = rowp(y - 1);
-    gx = ddx(m[t + 1], m[t - 1], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
-    gy = ddy(n[t], s[t], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
+    return ddx(m[t + 1], m[t - 1], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
+}
+template <typename Row>
+__device__ __forceinline__ float ddy_at(Row rowp, int y, int t) {
+    const float* n = rowp(y + 1);
+    const float* s = rowp(y - 1);
+    return ddy(n[t], s[t], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
 }
 
-template <bool VEC, Pass MODE>
+template <bool VEC, bool WALLS, Pass MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     k_chain(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, const int rows,
             FieldOut fo, unsigned* __restrict__ flag, double* __restrict__ partials) {
     extern __shared__ __align__(16) float smem[];
     Rings R{smem, smem + kPopFloats, smem + kPopFloats + kAFloats, smem + kPopFloats + kAFloats + kBFloats};
+    const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
 
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny;
-    const bool walls = P.wall_y != 0;
     const size_t plane = static_cast<size_t>(nx) * ny;
     const int x0 = blockIdx.x * kTileX;
     const int y0 = blockIdx.y * rows;
@@ -145,21 +190,28 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int s_first = y0 - 4;
     const int s_last = y_end + 3;
     const int iters = (y_end - y0) + 8;
-    auto row_ok = [&](int r) { return !walls || (r >= 0 && r < ny); };
+    auto row_ok = [&](int r) { return !WALLS || (r >= 0 && r < ny); };
+
+    CopyPlan<VEC> plan;
+    plan.init(x0, nx, plane);
+    auto issue_row = [&](int row) {
+        const unsigned ring_row = pop_addr + static_cast<unsigned>((row & (kRing - 1)) * kPlanes * kWin * 4);
+        plan.issue(ring_row, src + static_cast<size_t>(wrap(row, ny)) * nx);
+    };
 
     // diagnostics accumulators (Pass::Diag)
     double acc_r = 0.0, acc_b = 0.0, acc_jx = 0.0, acc_jy = 0.0, acc_u2 = 0.0, acc_bad = 0.0;
 
-    if (row_ok(s_first)) issue_row<VEC>(R, src, s_first, x0, nx, ny, plane);
+    if (row_ok(s_first)) issue_row(s_first);
     cp_commit();
-    if (row_ok(s_first + 1)) issue_row<VEC>(R, src, s_first + 1, x0, nx, ny, plane);
+    if (row_ok(s_first + 1)) issue_row(s_first + 1);
     cp_commit();
 
     for (int k = 0; k < iters; ++k) {
         const int s = s_first + k;
         cp_wait<1>();
         __syncthreads();
-        if (s + 2 <= s_last && row_ok(s + 2)) issue_row<VEC>(R, src, s + 2, x0, nx, ny, plane);
+        if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2);
         cp_commit();
 
         // ---------------- stage A: moments at row ya = s - 1 (tile + 3 halo)
@@ -167,30 +219,28 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int ya = s - 1;
             if (ya >= y0 - 3 && ya <= y_end + 2 && row_ok(ya) && t >= 1 && t < kWin - 1) {
                 float fr[9], fb[9];
-                gather(R, ya, t, walls, ny, fr, fb);
-                float rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    rr += fr[i];
-                    rb += fb[i];
-                    const float f = fr[i] + fb[i];
-                    if (lcx(i) != 0) jx += float(lcx(i)) * f;
-                    if (lcy(i) != 0) jy += float(lcy(i)) * f;
-                }
+                gather<WALLS>(R, ya, t, ny, fr, fb);
+                const float rr = sum9(fr);
+                const float rb = sum9(fb);
+                // colour-blind momentum sum_i f_i c_i (Eq. equ_u_def)
+                const float jx = ((fr[1] + fb[1]) + (fr[7] + fb[7])) + (fr[8] + fb[8]) -
+                                 (((fr[3] + fb[3]) + (fr[5] + fb[5])) + (fr[4] + fb[4]));
+                const float jy = ((fr[1] + fb[1]) + (fr[3] + fb[3])) + (fr[2] + fb[2]) -
+                                 (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
                 const float a = rr * P.inv_rho0_r;
                 const float b = rb * P.inv_rho0_b;
-                const float rn = (a - b) / (a + b);          // Eq. equ_rhoN_def
-                const float phip = P.phip_r * rr + P.phip_b * rb;  // App. A, Phi'
+                const float rn = (a - b) * rcp(a + b);             // Eq. equ_rhoN_def
+                const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
                 R.A(ya, 0)[t] = rn;
                 R.A(ya, 1)[t] = phip;
                 R.A(ya, 2)[t] = rr + rb;
                 R.A(ya, 3)[t] = jx;
                 R.A(ya, 4)[t] = jy;
-                if (walls && ya == 0) {  // even mirror beyond y = -1/2
+                if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
                     R.A(-1, 0)[t] = rn;
                     R.A(-1, 1)[t] = phip;
                 }
-                if (walls && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
+                if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
                     R.A(ny, 0)[t] = rn;
                     R.A(ny, 1)[t] = phip;
                 }
@@ -202,10 +252,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         {
             const int yb = s - 2;
             if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-                float gx, gy;
-                grad_at([&](int r) { return R.A(r, 0); }, yb, t, gx, gy);
+                auto rn_row = [&](int r) { return R.A(r, 0); };
+                const float gx = ddx_at(rn_row, yb, t);
+                const float gy = ddy_at(rn_row, yb, t);
                 // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
-                const float mag2 = gx * gx + gy * gy;
+                const float mag2 = fmaf(gx, gx, gy * gy);
                 const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
                 const float nhx = -gx * inv;
                 const float nhy = -gy * inv;
@@ -213,11 +264,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                 R.B(yb, 1)[t] = gy;
                 R.B(yb, 2)[t] = nhx;
                 R.B(yb, 3)[t] = nhy;
-                if (walls && yb == 0) {  // reflected normal beyond the wall
+                if (WALLS && yb == 0) {  // reflected normal beyond the wall
                     R.B(-1, 2)[t] = nhx;
                     R.B(-1, 3)[t] = -nhy;
                 }
-                if (walls && yb == ny - 1) {
+                if (WALLS && yb == ny - 1) {
                     R.B(ny, 2)[t] = nhx;
                     R.B(ny, 3)[t] = -nhy;
                 }
@@ -231,10 +282,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (yc >= y0 - 1 && yc <= y_end && row_ok(yc) && t >= 3 && t < kWin - 3) {
                 float K;
                 if (P.curvature_mode == 0) {
-                    float dnx, dny, unused;
-                    grad_at([&](int r) { return R.B(r, 2); }, yc, t, dnx, unused);
-                    grad_at([&](int r) { return R.B(r, 3); }, yc, t, unused, dny);
-                    K = dnx + dny;  // K = div n-hat (Sec. 2)
+                    // K = div n-hat (Sec. 2)
+                    K = ddx_at([&](int r) { return R.B(r, 2); }, yc, t) + ddy_at([&](int r) { return R.B(r, 3); }, yc, t);
                 } else {
                     K = P.fixed_K;
                 }
@@ -242,21 +291,22 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float gy = R.B(yc, 1)[t];
                 const float rho = R.A(yc, 2)[t];
                 // G = sigma K grad rho^N / 2 + rho g_acc + g_vol (Eq. equ_stforce plus body force)
-                const float Gx = P.half_sigma * K * gx + rho * P.gacc_x + P.gvol_x;
-                const float Gy = P.half_sigma * K * gy + rho * P.gacc_y + P.gvol_y;
-                const float inv_rho = 1.0f / rho;
+                const float hk = P.half_sigma * K;
+                const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
+                const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
+                const float inv_rho = rcp(rho);
                 // force-adjusted velocity (Eq. equ_u_def)
-                const float ux = (R.A(yc, 3)[t] + 0.5f * Gx) * inv_rho;
-                const float uy = (R.A(yc, 4)[t] + 0.5f * Gy) * inv_rho;
+                const float ux = fmaf(0.5f, Gx, R.A(yc, 3)[t]) * inv_rho;
+                const float uy = fmaf(0.5f, Gy, R.A(yc, 4)[t]) * inv_rho;
                 R.C(yc, 0)[t] = Gx;
                 R.C(yc, 1)[t] = Gy;
                 R.C(yc, 2)[t] = ux;
                 R.C(yc, 3)[t] = uy;
-                if (walls && yc == 0) {  // no-slip: odd mirror of u
+                if (WALLS && yc == 0) {  // no-slip: odd mirror of u
                     R.C(-1, 2)[t] = -ux;
                     R.C(-1, 3)[t] = -uy;
                 }
-                if (walls && yc == ny - 1) {
+                if (WALLS && yc == ny - 1) {
                     R.C(ny, 2)[t] = -ux;
                     R.C(ny, 3)[t] = -uy;
                 }
@@ -269,15 +319,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int yd = s - 4;
             const int gxo = x0 + t - kHalo;
             if (yd >= y0 && yd < y_end && t >= kHalo && t < kWin - kHalo && gxo < nx) {
-                float fr[9], fb[9];
-                gather(R, yd, t, walls, ny, fr, fb);
-                float rr = 0.f, rb = 0.f, f[9];
+                float fr[9], fb[9], f[9];
+                gather<WALLS>(R, yd, t, ny, fr, fb);
+                const float rr = sum9(fr);
+                const float rb = sum9(fb);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    rr += fr[i];
-                    rb += fb[i];
-                    f[i] = fr[i] + fb[i];
-                }
+                for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
                 const float rho = rr + rb;
                 const float ux = R.C(yd, 2)[t];
                 const float uy = R.C(yd, 3)[t];
@@ -285,76 +332,102 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (!isfinite(rho)) atomicOr(flag, 1u);
                     const float Gx = R.C(yd, 0)[t];
                     const float Gy = R.C(yd, 1)[t];
-                    float dPx, dPy, dux, duy, unused;
-                    grad_at([&](int r) { return R.A(r, 1); }, yd, t, dPx, dPy);
-                    grad_at([&](int r) { return R.C(r, 2); }, yd, t, dux, unused);
-                    grad_at([&](int r) { return R.C(r, 3); }, yd, t, unused, duy);
-                    const float divu = dux + duy;
-                    const float inv_rho = 1.0f / rho;
+                    auto phip_row = [&](int r) { return R.A(r, 1); };
+                    const float dPx = ddx_at(phip_row, yd, t);
+                    const float dPy = ddy_at(phip_row, yd, t);
+                    const float divu = ddx_at([&](int r) { return R.C(r, 2); }, yd, t) +
+                                       ddy_at([&](int r) { return R.C(r, 3); }, yd, t);
+                    const float inv_rho = rcp(rho);
                     // local shear eigenvalue (Sec. 2: nu(rho^N) = (2/lambda_3 - 1)/6)
                     float nu;
                     if (P.visc_mode == 0) {
                         const float rn = R.A(yd, 0)[t];
-                        nu = 0.5f * P.nu_r * (1.0f + rn) + 0.5f * P.nu_b * (1.0f - rn);
+                        nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
                     } else {
                         nu = P.eta * inv_rho;
                     }
-                    const float lam3 = 2.0f / (6.0f * nu + 1.0f);
-                    const float a = 1.0f - 0.5f * lam3;
+                    const float lam3 = 2.0f * rcp(fmaf(6.0f, nu, 1.0f));
+                    const float a = fmaf(-0.5f, lam3, 1.0f);
                     // correction tensor C_ab (App. A, Eq. Correction)
-                    const float iso = ux * dPx + uy * dPy - rho * divu * (1.0f / 3.0f);
-                    const float Cxx = a * (2.0f * ux * (Gx - dPx) - iso);
-                    const float Cyy = a * (2.0f * uy * (Gy - dPy) - iso);
-                    const float Cxy = a * (ux * (Gy - dPy) + uy * (Gx - dPx));
-                    // modes m = M f that relax (Table 1, rows 3..8; unweighted)
-                    float pxx = 0.f, pyy = 0.f, pxy = 0.f, gN = 0.f, gJx = 0.f, gJy = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        if (lcx(i) != 0) pxx += f[i];
-                        if (lcy(i) != 0) pyy += f[i];
-                        if (lcx(i) * lcy(i) != 0) pxy += float(lcx(i) * lcy(i)) * f[i];
-                        gN += lg(i) * f[i];
-                        if (lcx(i) != 0) gJx += lg(i) * float(lcx(i)) * f[i];
-                        if (lcy(i) != 0) gJy += lg(i) * float(lcy(i)) * f[i];
-                    }
-                    // equilibria h^(p).f^(0) (App. A) and sources S^(p)
-                    const float pres = P.cs2_r * rr + P.cs2_b * rb;
-                    const float Neq = (P.ghost_N_mode == 0) ? (P.neq_r * rr + P.neq_b * rb) : 0.0f;
-                    float dm[9];
-                    dm[0] = 0.0f;
-                    dm[1] = Gx;
-                    dm[2] = Gy;
-                    dm[3] = lam3 * (pres + rho * ux * ux - pxx) + Cxx;
-                    dm[4] = lam3 * (pres + rho * uy * uy - pyy) + Cyy;
-                    dm[5] = lam3 * (rho * ux * uy - pxy) + Cxy;
-                    dm[6] = P.lambda6 * (Neq - gN);
-                    dm[7] = -P.lambda7 * gJx;
-                    dm[8] = -P.lambda7 * gJy;
-                    // recolour (Eq. eq_re_color): red along e = grad rho^N/|grad rho^N| = -n-hat
+                    const float qx = Gx - dPx, qy = Gy - dPy;
+                    const float iso = fmaf(ux, dPx, fmaf(uy, dPy, -rho * divu * (1.0f / 3.0f)));
+                    const float Cxx = a * fmaf(2.0f * ux, qx, -iso);
+                    const float Cyy = a * fmaf(2.0f * uy, qy, -iso);
+                    const float Cxy = a * fmaf(ux, qy, uy * qx);
+                    // modes that relax (Table 1 rows 3..8, unweighted): Pi_xx, Pi_yy, Pi_xy, N, J_x, J_y
+                    const float dsum = (f[1] + f[5]) + (f[3] + f[7]);  // diagonals
+                    const float ax = f[4] + f[8], ay = f[2] + f[6];
+                    const float pxx = dsum + ax;
+                    const float pyy = dsum + ay;
+                    const float pxy = (f[1] + f[5]) - (f[3] + f[7]);
+                    const float gN = fmaf(lg(1), dsum, fmaf(lg(2), ax + ay, f[0]));
+                    const float gJx = fmaf(lg(1), (f[1] + f[7]) - (f[3] + f[5]), lg(8) * (f[8] - f[4]));
+                    const float gJy = fmaf(lg(1), (f[1] + f[3]) - (f[5] + f[7]), lg(2) * (f[2] - f[6]));
+                    // dm = lambda (m^(0) - m) + S with the equilibria h^(p).f^(0) and
+                    // sources S^(p) of App. A (S^(1,2) = G, S^(3..5) = C)
+                    const float pres = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+                    const float Neq = (P.ghost_N_mode == 0) ? fmaf(P.neq_r, rr, P.neq_b * rb) : 0.0f;
+                    const float rux = rho * ux;
+                    const float dm1 = Gx, dm2 = Gy;
+                    const float dm3 = fmaf(lam3, fmaf(rux, ux, pres) - pxx, Cxx);
+                    const float dm4 = fmaf(lam3, fmaf(rho * uy, uy, pres) - pyy, Cyy);
+                    const float dm5 = fmaf(lam3, fmaf(rux, uy, -pxy), Cxy);
+                    const float dm6 = P.lambda6 * (Neq - gN);
+                    const float dm7 = -P.lambda7 * gJx;
+                    const float dm8 = -P.lambda7 * gJy;
+                    // f+ - f = M^{-1} dm (App. A, Eq. eq84), grouped by parity of k^(p)
+                    float df[9];
+                    df[0] = fmaf(kinv(0, 3), dm3 + dm4, kinv(0, 6) * dm6);
+                    const float ex8 = fmaf(kinv(8, 3), dm3, fmaf(kinv(8, 4), dm4, kinv(8, 6) * dm6));
+                    const float ox8 = fmaf(kinv(8, 1), dm1, kinv(8, 7) * dm7);
+                    const float ey2 = fmaf(kinv(2, 3), dm3, fmaf(kinv(2, 4), dm4, kinv(2, 6) * dm6));
+                    const float oy2 = fmaf(kinv(2, 2), dm2, kinv(2, 8) * dm8);
+                    df[8] = ex8 + ox8;
+                    df[4] = ex8 - ox8;
+                    df[2] = ey2 + oy2;
+                    df[6] = ey2 - oy2;
+                    const float ed = fmaf(kinv(1, 3), dm3 + dm4, kinv(1, 6) * dm6);
+                    const float exy = kinv(1, 5) * dm5;
+                    const float odx = fmaf(kinv(1, 1), dm1, kinv(1, 7) * dm7);
+                    const float ody = fmaf(kinv(1, 2), dm2, kinv(1, 8) * dm8);
+                    const float pe = ed + exy, me = ed - exy, q1 = odx + ody, q2 = odx - ody;
+                    df[1] = pe + q1;  // (+1, +1)
+                    df[5] = pe - q1;  // (-1, -1)
+                    df[7] = me + q2;  // (+1, -1)
+                    df[3] = me - q2;  // (-1, +1)
+                    // recolour (Eq. eq_re_color): red moves along e = grad rho^N / |grad rho^N| = -n-hat,
+                    // by beta phi_i rho_R rho_B / rho (e . c-hat_i); phi_i = w_i phim for i != 0
                     const float ex = -R.B(yd, 2)[t];
                     const float ey = -R.B(yd, 3)[t];
-                    const float aR = rr * inv_rho;
-                    const float aB = rb * inv_rho;
-                    const float phim = (P.kphi_r * rr + P.kphi_b * rb) * inv_rho;  // phi_i / w_i, i != 0
-                    const float seg = P.beta * rr * rb * inv_rho * phim;
+                    const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
+                    const float seg = P.beta * (rr * rb) * inv_rho * phim;
+                    // the minority colour is formed directly and the majority as the rest
+                    // of f+, so that R++ + B++ = f+ holds to one rounding of the majority
                     const bool red_major = rr >= rb;
+                    const float amin = (red_major ? rb : rr) * inv_rho;
+                    const float smin = red_major ? -seg : seg;  // minority's sign of the segregation term
+                    const float sx = smin * ex, sy = smin * ey;
+                    float dmin[9];
+                    dmin[0] = 0.0f;
+                    dmin[8] = lw(8) * sx;
+                    dmin[4] = -dmin[8];
+                    dmin[2] = lw(2) * sy;
+                    dmin[6] = -dmin[2];
+                    const float dd1 = lw(1) * chx(1) * (sx + sy);
+                    const float dd3 = lw(3) * chx(1) * (sy - sx);
+                    dmin[1] = dd1;
+                    dmin[5] = -dd1;
+                    dmin[3] = dd3;
+                    dmin[7] = -dd3;
                     const size_t o = static_cast<size_t>(yd) * nx + gxo;
+                    float* out_min = dst + o + (red_major ? 9 * plane : 0);
+                    float* out_maj = dst + o + (red_major ? 0 : 9 * plane);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        float df = 0.0f;
-#pragma unroll
-                        for (int p = 1; p < 9; ++p) {
-                            if (kinv(i, p) != 0.0f) df = fmaf(kinv(i, p), dm[p], df);
-                        }
-                        const float fp = f[i] + df;  // f+ = f + M^{-1} dm
-                        float d = 0.0f;
-                        if (i != 0) d = seg * lw(i) * (chx(i) * ex + chy(i) * ey);
-                        // the minority colour directly, the majority as the rest of f+,
-                        // so that R++ + B++ = f+ holds to one rounding of the majority
-                        const float r_pp = fmaf(aR, fp, d);
-                        const float b_pp = fmaf(aB, fp, -d);
-                        dst[i * plane + o] = red_major ? fp - b_pp : r_pp;
-                        dst[(9 + i) * plane + o] = red_major ? b_pp : fp - r_pp;
+                        const float fp = f[i] + df[i];  // f+ = f + M^{-1} dm
+                        const float cmin = fmaf(amin, fp, dmin[i]);
+                        __stcs(out_min + i * plane, cmin);
+                        __stcs(out_maj + i * plane, fp - cmin);
                     }
                 } else if (MODE == Pass::Fields) {
                     const size_t o = static_cast<size_t>(yd) * nx + gxo;
@@ -362,14 +435,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (fo.rho_b) fo.rho_b[o] = rb;
                     if (fo.ux) fo.ux[o] = ux;
                     if (fo.uy) fo.uy[o] = uy;
-                    if (fo.p) fo.p[o] = P.cs2_r * rr + P.cs2_b * rb;
+                    if (fo.p) fo.p[o] = fmaf(P.cs2_r, rr, P.cs2_b * rb);
                 } else {
-                    float jx = 0.f, jy = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        if (lcx(i) != 0) jx += float(lcx(i)) * f[i];
-                        if (lcy(i) != 0) jy += float(lcy(i)) * f[i];
-                    }
+                    const float jx = (f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]);
+                    const float jy = (f[1] + f[2] + f[3]) - (f[5] + f[6] + f[7]);
                     if (isfinite(rho)) {
                         acc_r += rr;
                         acc_b += rb;
@@ -449,23 +518,36 @@ __global__ void k_diag_reduce(const double* __restrict__ partials, int nblocks, 
     }
 }
 
+template <bool VEC, bool WALLS, Pass MODE>
+cudaError_t launch_one(const float* src, float* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
+                       double* partials, cudaStream_t s) {
+    // the shared-memory opt-in is per kernel and per device: set it once for each
+    static unsigned long long configured = 0;
+    const size_t smem = chain_smem_bytes();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(k_chain<VEC, WALLS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    k_chain<VEC, WALLS, MODE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(src, dst, P, rows, fo, flag,
+                                                                                    partials);
+    return cudaGetLastError();
+}
+
 template <Pass MODE>
 cudaError_t launch_chain(const float* src, float* dst, const StepParams& P, int rows, FieldOut fo,
                          unsigned* flag, double* partials, cudaStream_t s) {
     const bool vec = (P.nx % 4) == 0;
-    const size_t smem = chain_smem_bytes();
-    const dim3 grid = chain_grid(P.nx, P.ny, rows);
-    cudaError_t e;
-    if (vec) {
-        e = cudaFuncSetAttribute(k_chain<true, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_chain<true, MODE><<<grid, kThreads, smem, s>>>(src, dst, P, rows, fo, flag, partials);
-    } else {
-        e = cudaFuncSetAttribute(k_chain<false, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_chain<false, MODE><<<grid, kThreads, smem, s>>>(src, dst, P, rows, fo, flag, partials);
-    }
-    return cudaGetLastError();
+    const bool walls = P.wall_y != 0;
+    if (vec && walls) return launch_one<true, true, MODE>(src, dst, P, rows, fo, flag, partials, s);
+    if (vec) return launch_one<true, false, MODE>(src, dst, P, rows, fo, flag, partials, s);
+    if (walls) return launch_one<false, true, MODE>(src, dst, P, rows, fo, flag, partials, s);
+    return launch_one<false, false, MODE>(src, dst, P, rows, fo, flag, partials, s);
 }
 
 }  // namespace
@@ -474,6 +556,27 @@ size_t chain_smem_bytes() { return sizeof(float) * static_cast<size_t>(kSmemFloa
 
 dim3 chain_grid(int nx, int ny, int rows) {
     return dim3(static_cast<unsigned>((nx + kTileX - 1) / kTileX), static_cast<unsigned>((ny + rows - 1) / rows), 1);
+}
+
+int chain_rows(int nx, int ny, int sms) {
+    // Rows per CTA: each CTA spends (rows + 8) row-iterations (8 fill the
+    // pipeline), and the CTAs run in waves of (SMs x 2 resident CTAs); pick
+    // the segment length that minimises waves x (rows + 8).
+    const int strips = (nx + kTileX - 1) / kTileX;
+    const long slots = 2L * (sms > 0 ? sms : 1);
+    int best = 8;
+    long best_cost = -1;
+    for (int rows = 8; rows <= 512; rows += 8) {
+        const long segs = (ny + rows - 1) / rows;
+        const long waves = (strips * segs + slots - 1) / slots;
+        const long cost = waves * (rows + 8);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = rows;
+        }
+        if (rows >= ny) break;
+    }
+    return best;
 }
 
 cudaError_t launch_step(const float* src, float* dst, const StepParams& P, int rows, unsigned* flag,
