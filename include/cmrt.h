@@ -161,6 +161,31 @@ int64_t cmrt_launch_count(const cmrt_ctx* c);
 /* Bytes of device memory the context holds. */
 size_t cmrt_device_bytes(const cmrt_ctx* c);
 
+/* Diagnostics of caller-owned populations that allocate nothing.
+ *
+ * The paper has no counterpart: this is a library facility.  It is for
+ * callers that cannot allocate device memory when they need the reduction:
+ * code recording a CUDA graph, code under a hard device-memory cap or a
+ * custom allocator, code that must not let cudaMalloc/cudaFree synchronise
+ * the device.  It needs no context and calls no allocating routine.
+ *
+ * p:     parameters of the lattice (validated as for cmrt_init).
+ * pops:  pre-collision populations float[2][9][ny][nx] in DEVICE memory of
+ *        the current device (e.g. from cmrt_get_populations); host memory is
+ *        rejected with CMRT_EINVAL, since copying it would need a buffer.
+ * out:   host double[6], the same quantities as cmrt_diagnostics.
+ * cuda_stream: stream the reduction runs on; the call synchronises it.
+ *
+ * Scratch: a fixed area compiled into the library (384 KiB of device memory
+ * on every GPU that loads it, held until exit) with room for 8192 partial
+ * blocks, i.e. lattices up to 983,040 columns wide and any height.  Wider
+ * lattices are rejected with CMRT_EINVAL.  All calls share that area: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The first call on a device looks up the
+ * area's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Returns CMRT_ENONFINITE when out[5] > 0. */
+cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const float* pops, double out[6], void* cuda_stream);
+
 /* Frees the context and everything it allocated.  NULL is a no-op. */
 void cmrt_destroy(cmrt_ctx* c);
 

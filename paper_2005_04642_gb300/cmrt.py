@@ -53,6 +53,8 @@ _SIGNATURES = [
     ("cmrt_time", ctypes.c_int64, [ctypes.c_void_p]),
     ("cmrt_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
     ("cmrt_device_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("cmrt_diagnostics_noalloc", ctypes.c_int, [ctypes.POINTER(cmrt_params), ctypes.c_void_p,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("cmrt_destroy", None, [ctypes.c_void_p]),
     ("cmrt_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -162,6 +164,15 @@ def cmrt_launch_count(ctx):
 
 def cmrt_device_bytes(ctx):
     return load().cmrt_device_bytes(ctx)
+
+
+def cmrt_diagnostics_noalloc(params: cmrt_params, pops_ptr: int, stream_ptr: int = 0):
+    """Diagnostics of device populations without any allocation (six floats)."""
+    out = (ctypes.c_double * 6)()
+    st = load().cmrt_diagnostics_noalloc(ctypes.byref(params), pops_ptr, out, stream_ptr or None)
+    vals = list(out)
+    _check(st)
+    return vals
 
 
 def cmrt_destroy(ctx):

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "cmrt.h"
@@ -485,3 +486,92 @@ const char* cmrt_last_error(const cmrt_ctx* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Diagnostics without any allocation.
+//
+// Some callers cannot allocate device memory at the point where they want a
+// reduction of the state: code recording a CUDA graph (cudaMalloc is not a
+// capturable operation), code running under a hard device-memory cap or a
+// custom allocator that forbids ad-hoc allocations, and code that must not
+// let cudaMalloc/cudaFree synchronise the device in the middle of a pipeline.
+// For them this entry point works on caller-owned populations and uses a
+// fixed scratch area compiled into the library instead of a context.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Per-CTA FP64 partial sums, then the reduced result in the last slot.
+// Sized for up to kNoAllocMaxBlocks CTAs of the diagnostics pass; every GPU
+// that loads the library holds these 384 KiB until the process exits.
+constexpr int kNoAllocMaxBlocks = 8192;
+static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocMaxBlocks + 1) * cmrt::kDiagSlots];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const float* pops, double out[6],
+                                                void* cuda_stream) {
+    cmrt_status st = validate(p);
+    if (st != CMRT_OK) return st;
+    if (!pops || !out) return fail(nullptr, CMRT_EINVAL, "pops and out must not be NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return fail(nullptr, CMRT_ECUDA, "no usable current CUDA device");
+    }
+    double* scratch = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side name
+        // of a __device__ array is not its device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr)
+                return fail(nullptr, CMRT_ECUDA, "cudaGetSymbolAddress of the scratch area failed: %s",
+                            cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    if (!is_device_ptr(pops)) return fail(nullptr, CMRT_EINVAL, "pops must be device memory of the current device");
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    const int strips = (p->nx + cmrt::kTileX - 1) / cmrt::kTileX;
+    if (strips > kNoAllocMaxBlocks)
+        return fail(nullptr, CMRT_EINVAL, "nx = %d needs %d column strips; the scratch area holds %d", p->nx, strips,
+                    kNoAllocMaxBlocks);
+    int rows = cmrt::chain_rows(p->nx, p->ny, sms);
+    const int max_segs = kNoAllocMaxBlocks / strips;
+    if ((p->ny + rows - 1) / rows > max_segs) rows = (p->ny + max_segs - 1) / max_segs;
+    const dim3 g = cmrt::chain_grid(p->nx, p->ny, rows);
+    const int nblocks = static_cast<int>(g.x * g.y);
+    if (nblocks > kNoAllocMaxBlocks)
+        return fail(nullptr, CMRT_EINVAL, "lattice %d x %d needs %d partial blocks; the scratch area holds %d", p->nx,
+                    p->ny, nblocks, kNoAllocMaxBlocks);
+    const StepParams sp = derive(*p);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double* result = scratch + static_cast<size_t>(kNoAllocMaxBlocks) * cmrt::kDiagSlots;
+    // every partial slot used below is written by its CTA and the result by the
+    // reduction, so nothing left from an earlier call is read
+    CK(nullptr, cmrt::launch_diag_partials_pre(pops, sp, rows, scratch, s));
+    CK(nullptr, cmrt::launch_diag_reduce(scratch, nblocks, result, s));
+    double h6[cmrt::kDiagSlots];
+    CK(nullptr, cudaMemcpyAsync(h6, result, sizeof h6, cudaMemcpyDeviceToHost, s));
+    CK(nullptr, cudaStreamSynchronize(s));
+    out[0] = h6[0];
+    out[1] = h6[1];
+    out[2] = h6[2];
+    out[3] = h6[3];
+    out[4] = std::sqrt(h6[4]);
+    out[5] = h6[5];
+    if (h6[5] > 0) return fail(nullptr, CMRT_ENONFINITE, "%.0f nodes have a non-finite density", h6[5]);
+    return CMRT_OK;
+}
+

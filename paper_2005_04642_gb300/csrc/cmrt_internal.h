@@ -66,6 +66,9 @@ cudaError_t launch_fields(const float* src, const StepParams& P, int rows, Field
 // Per-CTA FP64 partial diagnostics into partials[grid][kDiagSlots].
 cudaError_t launch_diag_partials(const float* src, const StepParams& P, int rows,
                                  double* partials, cudaStream_t s);
+// Same, from pre-collision populations in the public layout float[2][9][ny][nx].
+cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int rows,
+                                     double* partials, cudaStream_t s);
 // Reduces nblocks partial rows into out[kDiagSlots] (one CTA).
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s);
 

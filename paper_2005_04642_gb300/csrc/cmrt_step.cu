@@ -139,12 +139,17 @@ struct CopyPlan {
 // Pre-collision populations at (row y, window column t): pull from the
 // post-collision ring, f_i(r) = P_i(r - c_i) (Eq. equ_evolution), with
 // half-way bounce-back P_opp(i)(r) where r - c_i lies beyond a wall.
-template <bool WALLS>
+// With PRE the rows hold pre-collision populations f(t) already in place
+// (the public layout), so the node's own column is read unshifted.
+template <bool WALLS, bool PRE = false>
 __device__ __forceinline__ void gather(const Rings& R, int y, int t, int ny, float (&fr)[9], float (&fb)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sy = y - lcy(i);
-        if (WALLS && (sy < 0 || sy >= ny)) {
+        if (PRE) {
+            fr[i] = R.P(y, i)[t];
+            fb[i] = R.P(y, 9 + i)[t];
+        } else if (WALLS && (sy < 0 || sy >= ny)) {
             fr[i] = R.P(y, lopp(i))[t];
             fb[i] = R.P(y, 9 + lopp(i))[t];
         } else {
@@ -173,7 +178,7 @@ __device__ __forceinline__ float ddy_at(Row rowp, int y, int t) {
     return ddy(n[t], s[t], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
 }
 
-template <bool VEC, bool WALLS, Pass MODE>
+template <bool VEC, bool WALLS, Pass MODE, bool PRE = false>
 __global__ void __launch_bounds__(kThreads, 2)
     k_chain(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, const int rows,
             FieldOut fo, unsigned* __restrict__ flag, double* __restrict__ partials) {
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int ya = s - 1;
             if (ya >= y0 - 3 && ya <= y_end + 2 && row_ok(ya) && t >= 1 && t < kWin - 1) {
                 float fr[9], fb[9];
-                gather<WALLS>(R, ya, t, ny, fr, fb);
+                gather<WALLS, PRE>(R, ya, t, ny, fr, fb);
                 const float rr = sum9(fr);
                 const float rb = sum9(fb);
                 // colour-blind momentum sum_i f_i c_i (Eq. equ_u_def)
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int gxo = x0 + t - kHalo;
             if (yd >= y0 && yd < y_end && t >= kHalo && t < kWin - kHalo && gxo < nx) {
                 float fr[9], fb[9], f[9];
-                gather<WALLS>(R, yd, t, ny, fr, fb);
+                gather<WALLS, PRE>(R, yd, t, ny, fr, fb);
                 const float rr = sum9(fr);
                 const float rb = sum9(fb);
 #pragma unroll
@@ -518,7 +523,7 @@ __global__ void k_diag_reduce(const double* __restrict__ partials, int nblocks, 
     }
 }
 
-template <bool VEC, bool WALLS, Pass MODE>
+template <bool VEC, bool WALLS, Pass MODE, bool PRE = false>
 cudaError_t launch_one(const float* src, float* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
                        double* partials, cudaStream_t s) {
     // the shared-memory opt-in is per kernel and per device: set it once for each
@@ -529,12 +534,12 @@ cudaError_t launch_one(const float* src, float* dst, const StepParams& P, int ro
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(k_chain<VEC, WALLS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_chain<VEC, WALLS, MODE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    k_chain<VEC, WALLS, MODE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(src, dst, P, rows, fo, flag,
+    k_chain<VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(src, dst, P, rows, fo, flag,
                                                                                     partials);
     return cudaGetLastError();
 }
@@ -591,6 +596,17 @@ cudaError_t launch_fields(const float* src, const StepParams& P, int rows, Field
 cudaError_t launch_diag_partials(const float* src, const StepParams& P, int rows, double* partials,
                                  cudaStream_t s) {
     return launch_chain<Pass::Diag>(src, nullptr, P, rows, FieldOut{}, nullptr, partials, s);
+}
+
+cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int rows, double* partials,
+                                     cudaStream_t s) {
+    const bool vec = (P.nx % 4) == 0;
+    const bool walls = P.wall_y != 0;
+    const FieldOut none{};
+    if (vec && walls) return launch_one<true, true, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
+    if (vec) return launch_one<true, false, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
+    if (walls) return launch_one<false, true, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
+    return launch_one<false, false, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
 }
 
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s) {
