@@ -271,6 +271,8 @@ def run_cmrt(args, rank, world, local_rank):
     h2d = (h_rn.numel() + h_u.numel()) * 4
     d2h = sum(o.numel() for o in h_out) * 4
 
+    variants = run_variants(args, cm, I, stream, ms / args.steps) if (args.variants and rank == 0) else None
+
     if rank != 0:
         if dist is not None:
             dist.barrier()
@@ -296,12 +298,60 @@ def run_cmrt(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps,
                     "what": "cmrt_init from pinned host rho^N_0, u_0 + K steps + cmrt_fields into pinned host buffers"},
-            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "variants": variants,
             "check": {"mass_r": diag["mass_r"], "mass_b": diag["mass_b"], "nonfinite": diag["nonfinite"]}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def time_steps(cm, d, rn, u, steps, warmup, stream):
+    """ms per step (CUDA events on the launching stream) of a device-resident lattice."""
+    import torch
+    lat = cm.Lattice(d, torch.from_numpy(np.ascontiguousarray(rn, dtype=np.float32)).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda(), stream=stream)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    diag = lat.diagnostics()
+    lat.close()
+    torch.cuda.empty_cache()
+    return ms, diag
+
+
+def run_variants(args, cm, I, stream, fp32_ms):
+    """The reduced-precision storage forms on the same workload and on the
+    16384 x 8192 buoyant-drops field (walls, gravity), each against FP32 there."""
+    peak, _ = measured_peak_hbm()
+    out = {}
+    d, rn, u = make_workload(args.side)
+    cells = d["nx"] * d["ny"]
+    steps = max(20, args.steps // 4)
+    for name, prec, nbytes in (("fp16", 2, 88), ("bf16", 1, 88)):
+        ms, _ = time_steps(cm, dict(d, precision=prec), rn, u, steps, 5, stream)
+        out[f"{name}_{WORKLOAD if args.side == N_SIDE else args.side}"] = {
+            "value": cells / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "speedup_vs_fp32": fp32_ms / ms,
+            "bytes_per_cell": nbytes, "achieved_GBs": nbytes * cells / (ms * 1e-3) / 1e9,
+            "frac_of_hbm_peak": nbytes * cells / (ms * 1e-3) / 1e9 / peak, "steps": steps}
+    if args.side == N_SIDE:
+        d, rn, u = I.buoyant_drops()
+        cells = d["nx"] * d["ny"]
+        base = None
+        for name, prec, nbytes in (("fp32", 0, 144), ("fp16", 2, 88), ("bf16", 1, 88)):
+            ms, diag = time_steps(cm, dict(d, precision=prec), rn, u, steps, 5, stream)
+            base = base or ms
+            out[f"{name}_buoyant_16384x8192_walls_256drops"] = {
+                "value": cells / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "speedup_vs_fp32": base / ms,
+                "bytes_per_cell": nbytes, "achieved_GBs": nbytes * cells / (ms * 1e-3) / 1e9,
+                "frac_of_hbm_peak": nbytes * cells / (ms * 1e-3) / 1e9 / peak, "steps": steps,
+                "nonfinite": diag["nonfinite"]}
+    return out
 
 
 def main():
@@ -311,6 +361,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="cmrt", choices=["cmrt", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the reduced-precision timings reported under 'variants'")
     ap.add_argument("--side", type=int, default=N_SIDE,
                     help="lattice side; smaller sides (same drop density) are for profiling captures")
     args = ap.parse_args()

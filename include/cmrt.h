@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define CMRT_ABI_VERSION 1
+#define CMRT_ABI_VERSION 2
 
 typedef struct cmrt_ctx cmrt_ctx; /* opaque, owned by the library */
 
@@ -86,9 +86,13 @@ typedef struct {
     int32_t curvature_mode;  /* 0: K = div n-hat; 1: K = fixed_K (Sec. 4.2)                        */
     double fixed_K;
     int32_t ghost_N_mode;    /* 0: N relaxes to h^(6).f^(0) (App. A); 1: N relaxes to 0 (Table 1) */
-    int32_t precision;       /* population storage: 0 = FP32 (the only one built)                 */
+    int32_t precision;       /* population storage in HBM: 0 = FP32 (72 B/node); 1 = BF16, 2 = FP16
+                                (44 B/node: rho_R, rho_B in FP32 plus nine 16-bit pairs of
+                                deviations C_i - rho_C psi^C_i); arithmetic is FP32 in all cases */
     int32_t diag_every;      /* cmrt_step checks the non-finite flag every diag_every steps
                                 (synchronising the stream then); 0 = only at cmrt_diagnostics    */
+    int32_t precision_reference; /* 16-bit storage reference psi^C_i: 0 = phi_i of pure colour C
+                                (Eq. eq_phi at alpha_C); 1 = the lattice weights w_i            */
 } cmrt_params;
 
 /* ABI version of the loaded library (CMRT_ABI_VERSION). */

@@ -21,7 +21,7 @@ struct Ctx {
     StepParams sp{};
     int device = 0;
     cudaStream_t stream = nullptr;
-    float* buf[2] = {nullptr, nullptr};  // post-collision populations, A/B
+    void* buf[2] = {nullptr, nullptr};   // post-collision state, A/B (layout of p.precision)
     int cur = 0;                         // buf[cur] holds P_{t-1}
     unsigned* d_flag = nullptr;          // non-finite flag written by the step kernel
     double* d_partials = nullptr;        // per-CTA partial diagnostics
@@ -104,7 +104,10 @@ cmrt_status validate(const cmrt_params* p) {
     if (!finite(p->fixed_K)) return fail(nullptr, CMRT_EINVAL, "fixed_K must be finite");
     if (p->ghost_N_mode != 0 && p->ghost_N_mode != 1)
         return fail(nullptr, CMRT_EINVAL, "ghost_N_mode must be 0 or 1");
-    if (p->precision != 0) return fail(nullptr, CMRT_EINVAL, "precision %d is not built (only FP32 = 0 is)", p->precision);
+    if (p->precision < 0 || p->precision > 2)
+        return fail(nullptr, CMRT_EINVAL, "precision must be 0 (FP32), 1 (BF16) or 2 (FP16)");
+    if (p->precision_reference != 0 && p->precision_reference != 1)
+        return fail(nullptr, CMRT_EINVAL, "precision_reference must be 0 or 1");
     if (p->diag_every < 0) return fail(nullptr, CMRT_EINVAL, "diag_every must be >= 0");
     return CMRT_OK;
 }
@@ -144,6 +147,24 @@ StepParams derive(const cmrt_params& p) {
     s.gvol_x = static_cast<float>(p.g_vol[0]);
     s.gvol_y = static_cast<float>(p.g_vol[1]);
     s.fixed_K = static_cast<float>(p.fixed_K);
+    s.precision = p.precision;
+    // 16-bit storage keeps C_i - rho_C psi^C_i.  Reference 0: the pure-colour
+    // rest weights phi_i of Eq. eq_phi at alpha_C; reference 1: w_i.
+    // The FP32 weights are adjusted so that psi_0 + 4 psi_axis + 4 psi_diag is
+    // exactly 1 in real arithmetic: any reference decodes correctly, but one
+    // whose weights do not sum to 1 would bias colour mass every step.
+    const double wts[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    auto weights = [&](double alpha, float out[3]) {
+        const double axis = p.precision_reference == 1 ? wts[1] : 1.8 * (1.0 - alpha) * wts[1];
+        const double diag = p.precision_reference == 1 ? wts[2] : 1.8 * (1.0 - alpha) * wts[2];
+        const double fa = static_cast<float>(axis);
+        const double moving = std::ldexp(std::nearbyint(std::ldexp(4.0 * fa + 4.0 * static_cast<float>(diag), 24)), -24);
+        out[1] = static_cast<float>(fa);
+        out[2] = static_cast<float>((moving - 4.0 * fa) / 4.0);   // exact: a multiple of 2^-30
+        out[0] = static_cast<float>(1.0 - moving);                // exact: a multiple of 2^-24
+    };
+    weights(p.alpha_r, s.psi_r);
+    weights(p.alpha_b, s.psi_b);
     return s;
 }
 
@@ -200,7 +221,7 @@ cmrt_status set_device(Ctx* c) {
 }
 
 void free_all(Ctx* c) {
-    for (float*& b : c->buf)
+    for (void*& b : c->buf)
         if (b) cudaFree(b), b = nullptr;
     if (c->d_flag) cudaFree(c->d_flag), c->d_flag = nullptr;
     if (c->d_partials) cudaFree(c->d_partials), c->d_partials = nullptr;
@@ -277,8 +298,8 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
         return bail(CMRT_ECUDA);
     }
     const size_t n = cells(*c);
-    const size_t state_bytes = n * 18 * sizeof(float);
-    for (float*& b : c->buf) {
+    const size_t state_bytes = n * cmrt::state_node_bytes(p->precision);
+    for (void*& b : c->buf) {
         cudaError_t e = cudaMalloc(&b, state_bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -293,7 +314,7 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
         cudaGetLastError();
         sms = 1;
     }
-    c->rows = cmrt::chain_rows(p->nx, p->ny, sms);
+    c->rows = cmrt::chain_rows(p->nx, p->ny, sms, p->precision);
     const dim3 g = cmrt::chain_grid(p->nx, p->ny, c->rows);
     c->n_partials = static_cast<int>(g.x * g.y);
     if (cudaMalloc(&c->d_flag, sizeof(unsigned)) != cudaSuccess ||
@@ -308,37 +329,49 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
         fail(c, CMRT_ECUDA, "cudaMemsetAsync failed");
         return bail(CMRT_ECUDA);
     }
-    // inputs: copy host arrays into staging
+    // inputs: copy host arrays into staging (after an FP32 state area when the
+    // state is stored in 16 bits and has to be encoded from FP32)
     const float* d_rn = rho_n0;
     const float* d_u = u0;
     const bool rn_host = rho_n0 && !is_device_ptr(rho_n0);
     const bool u_host = u0 && !is_device_ptr(u0);
-    if (rn_host || u_host) {
-        if (ensure_staging(c, n * 3 * sizeof(float)) != CMRT_OK) return bail(CMRT_ENOMEM);
+    const bool packed = p->precision != 0;
+    const size_t in_off = packed ? 18 * n : 0;
+    if (rn_host || u_host || packed) {
+        if (ensure_staging(c, (in_off + ((rn_host || u_host) ? 3 * n : 0)) * sizeof(float)) != CMRT_OK)
+            return bail(CMRT_ENOMEM);
         if (rn_host) {
-            if (cudaMemcpyAsync(c->staging, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            if (cudaMemcpyAsync(c->staging + in_off, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess) {
                 fail(c, CMRT_ECUDA, "copy of rho_n0 failed");
                 return bail(CMRT_ECUDA);
             }
-            d_rn = c->staging;
+            d_rn = c->staging + in_off;
         }
         if (u_host) {
-            if (cudaMemcpyAsync(c->staging + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            if (cudaMemcpyAsync(c->staging + in_off + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess) {
                 fail(c, CMRT_ECUDA, "copy of u0 failed");
                 return bail(CMRT_ECUDA);
             }
-            d_u = c->staging + n;
+            d_u = c->staging + in_off + n;
         }
     }
+    float* post32 = packed ? c->staging : static_cast<float*>(c->buf[0]);
     cudaError_t e = cmrt::launch_init_fp64(d_rn, d_u, p->nx, p->ny, p->wall_y, p->rho0_r, p->rho0_b, p->alpha_r,
-                                           p->alpha_b, c->buf[0], c->stream);
+                                           p->alpha_b, post32, c->stream);
+    if (e == cudaSuccess && packed) {
+        c->launches++;
+        e = cmrt::launch_encode(post32, c->sp, c->buf[0], c->stream);
+    }
     if (e != cudaSuccess) {
         fail(c, CMRT_ECUDA, "init kernel launch failed: %s", cudaGetErrorString(e));
         return bail(CMRT_ECUDA);
     }
     c->launches++;
-    if (rn_host || u_host) {
-        // host buffers may be reused by the caller as soon as we return
+    if (rn_host || u_host || packed) {
+        // host buffers may be reused by the caller as soon as we return, and the
+        // staging area by the next call
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
             fail(c, CMRT_ECUDA, "stream synchronisation failed");
             return bail(CMRT_ECUDA);
@@ -420,14 +453,21 @@ cmrt_status cmrt_get_populations(cmrt_ctx* h, float* dst) {
     if (!c) return CMRT_ESTATE;
     if (!dst) return fail(c, CMRT_EINVAL, "dst is NULL");
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
-    const size_t bytes = cells(*c) * 18 * sizeof(float);
+    const size_t n18 = cells(*c) * 18;
+    const size_t bytes = n18 * sizeof(float);
     const bool host = !is_device_ptr(dst);
-    float* d = dst;
-    if (host) {
-        if (ensure_staging(c, bytes) != CMRT_OK) return CMRT_ENOMEM;
-        d = c->staging;
+    const bool packed = c->p.precision != 0;
+    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (host dst)]
+    const size_t need = (packed ? n18 : 0) + (host ? n18 : 0);
+    if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+    const float* post32 = static_cast<const float*>(c->buf[c->cur]);
+    if (packed) {
+        CK(c, cmrt::launch_decode(c->buf[c->cur], c->sp, c->staging, c->stream));
+        c->launches++;
+        post32 = c->staging;
     }
-    CK(c, cmrt::launch_stream_out(c->buf[c->cur], c->sp, d, c->stream));
+    float* d = host ? c->staging + (packed ? n18 : 0) : dst;
+    CK(c, cmrt::launch_stream_out(post32, c->sp, d, c->stream));
     c->launches++;
     if (host) {
         CK(c, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -441,17 +481,27 @@ cmrt_status cmrt_set_populations(cmrt_ctx* h, const float* src) {
     if (!c) return CMRT_ESTATE;
     if (!src) return fail(c, CMRT_EINVAL, "src is NULL");
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
-    const size_t bytes = cells(*c) * 18 * sizeof(float);
+    const size_t n18 = cells(*c) * 18;
+    const size_t bytes = n18 * sizeof(float);
     const float* s = src;
     const bool host = !is_device_ptr(src);
+    const bool packed = c->p.precision != 0;
+    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (host src)]
+    const size_t need = (packed ? n18 : 0) + (host ? n18 : 0);
+    if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
     if (host) {
-        if (ensure_staging(c, bytes) != CMRT_OK) return CMRT_ENOMEM;
-        CK(c, cudaMemcpyAsync(c->staging, src, bytes, cudaMemcpyHostToDevice, c->stream));
-        s = c->staging;
+        float* hs = c->staging + (packed ? n18 : 0);
+        CK(c, cudaMemcpyAsync(hs, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        s = hs;
     }
-    CK(c, cmrt::launch_unstream_in(s, c->sp, c->buf[c->cur], c->stream));
+    float* post32 = packed ? c->staging : static_cast<float*>(c->buf[c->cur]);
+    CK(c, cmrt::launch_unstream_in(s, c->sp, post32, c->stream));
     c->launches++;
-    if (host) CK(c, cudaStreamSynchronize(c->stream));
+    if (packed) {
+        CK(c, cmrt::launch_encode(post32, c->sp, c->buf[c->cur], c->stream));
+        c->launches++;
+    }
+    if (host || packed) CK(c, cudaStreamSynchronize(c->stream));
     return CMRT_OK;
 }
 
@@ -547,7 +597,7 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
     if (strips > kNoAllocMaxBlocks)
         return fail(nullptr, CMRT_EINVAL, "nx = %d needs %d column strips; the scratch area holds %d", p->nx, strips,
                     kNoAllocMaxBlocks);
-    int rows = cmrt::chain_rows(p->nx, p->ny, sms);
+    int rows = cmrt::chain_rows(p->nx, p->ny, sms, 0);
     const int max_segs = kNoAllocMaxBlocks / strips;
     if ((p->ny + rows - 1) / rows > max_segs) rows = (p->ny + max_segs - 1) / max_segs;
     const dim3 g = cmrt::chain_grid(p->nx, p->ny, rows);

@@ -4,6 +4,9 @@
 // the paper at time t is the pre-collision f(t) = stream(P_{t-1})
 // (Eq. equ_evolution).  These kernels translate between the two, and build
 // the initial state from a colour field and a velocity field.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "cmrt_device.cuh"
 
 namespace cmrt {
@@ -113,6 +116,67 @@ __global__ void k_unstream_in(const float* __restrict__ pre, int nx, int ny, int
     }
 }
 
+// 16-bit storage (see cmrt_step.cu): a node keeps (rho'_R, rho'_B) in FP32 and,
+// per link, the deviations d_C,i = C_i - rho_C psi^C_i as a 16-bit pair, with
+// rho_C the sum of the record's own nine populations of colour C and
+// rho'_C = rho_C - sum_i round(d_C,i), so that decoding conserves rho_C.
+__device__ __forceinline__ float psi_of(const float (&psi)[3], int i) {
+    return i == 0 ? psi[0] : ((i & 1) ? psi[2] : psi[1]);
+}
+__device__ __forceinline__ unsigned pack2(float a, float b, int precision) {
+    if (precision == kPrecF16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned*>(&h);
+}
+__device__ __forceinline__ float2 unpack2(unsigned v, int precision) {
+    if (precision == kPrecF16) return __half22float2(*reinterpret_cast<const __half2*>(&v));
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
+}
+
+__global__ void k_encode(const float* __restrict__ post, StepParams P, char* __restrict__ state) {
+    const size_t nodes = static_cast<size_t>(P.nx) * P.ny;
+    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < nodes;
+         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float r[9], b[9], rr = 0.f, rb = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            r[i] = post[i * nodes + n];
+            b[i] = post[(9 + i) * nodes + n];
+            rr += r[i];
+            rb += b[i];
+        }
+        unsigned* dev = reinterpret_cast<unsigned*>(state + nodes * 8);
+        float er = 0.f, eb = 0.f;  // rounded deviations, absorbed by the stored densities
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const unsigned h = pack2(r[i] - rr * psi_of(P.psi_r, i), b[i] - rb * psi_of(P.psi_b, i), P.precision);
+            const float2 back = unpack2(h, P.precision);
+            er += back.x;
+            eb += back.y;
+            dev[i * nodes + n] = h;
+        }
+        reinterpret_cast<float2*>(state)[n] = make_float2(rr - er, rb - eb);
+    }
+}
+
+__global__ void k_decode(const char* __restrict__ state, StepParams P, float* __restrict__ post) {
+    const size_t nodes = static_cast<size_t>(P.nx) * P.ny;
+    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < nodes;
+         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float2 rho = reinterpret_cast<const float2*>(state)[n];
+        const unsigned* dev = reinterpret_cast<const unsigned*>(state + nodes * 8);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float2 d = unpack2(dev[i * nodes + n], P.precision);
+            post[i * nodes + n] = fmaf(rho.x, psi_of(P.psi_r, i), d.x);
+            post[(9 + i) * nodes + n] = fmaf(rho.y, psi_of(P.psi_b, i), d.y);
+        }
+    }
+}
+
 dim3 flat_grid(size_t n) {
     size_t blocks = (n + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
@@ -127,6 +191,16 @@ cudaError_t launch_init_fp64(const float* rho_n0, const float* u0, int nx, int n
                              double rho0_b, double alpha_r, double alpha_b, float* post, cudaStream_t s) {
     InitIn in{rho_n0, u0, rho0_r, rho0_b, alpha_r, alpha_b};
     k_init<<<flat_grid(static_cast<size_t>(nx) * ny), 256, 0, s>>>(in, nx, ny, walls, post);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const float* post32, const StepParams& P, void* state, cudaStream_t s) {
+    k_encode<<<flat_grid(static_cast<size_t>(P.nx) * P.ny), 256, 0, s>>>(post32, P, static_cast<char*>(state));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const void* state, const StepParams& P, float* post32, cudaStream_t s) {
+    k_decode<<<flat_grid(static_cast<size_t>(P.nx) * P.ny), 256, 0, s>>>(static_cast<const char*>(state), P, post32);
     return cudaGetLastError();
 }
 

@@ -10,8 +10,15 @@ namespace cmrt {
 
 // Parameters of one step in the form the kernels use: FP32 coefficients
 // derived once on the host (in FP64) from cmrt_params.
+// Population storage in HBM (cmrt_params.precision).
+constexpr int kPrecF32 = 0;
+constexpr int kPrecB16 = 1;
+constexpr int kPrecF16 = 2;
+
 struct StepParams {
     int nx, ny, wall_y;
+    int precision;                 // kPrecF32 / kPrecB16 / kPrecF16
+    float psi_r[3], psi_b[3];      // 16-bit storage reference weights (rest, axis, diagonal)
     int visc_mode, curvature_mode, ghost_N_mode;
     float inv_rho0_r, inv_rho0_b;  // colour index (Eq. equ_rhoN_def)
     float alpha_r, alpha_b;        // rest weights phi_0 (Eq. eq_phi)
@@ -49,28 +56,31 @@ enum class Pass : int { Step = 0, Fields = 1, Diag = 2 };
 // Number of FP64 partial sums each CTA of the diagnostics pass writes.
 constexpr int kDiagSlots = 6;  // mass_r, mass_b, mom_x, mom_y, max|u|^2, non-finite count
 
-size_t chain_smem_bytes();
+// Bytes of one node of the state for a storage precision (72 FP32, 44 16-bit).
+size_t state_node_bytes(int precision);
 // grid of the chain kernel for a lattice, with `rows` rows per CTA
 dim3 chain_grid(int nx, int ny, int rows);
 // rows per CTA chosen for a lattice on a device with `sms` multiprocessors
-int chain_rows(int nx, int ny, int sms);
+int chain_rows(int nx, int ny, int sms, int precision);
 
-// One fused step: src holds the post-collision populations P_{t-1}
-// (float[18][ny][nx]), dst receives P_t.  flag is set non-zero if a node has a
+// One fused step: src holds the post-collision state P_{t-1} in the layout of
+// P.precision, dst receives P_t.  flag is set non-zero if a node has a
 // non-finite density.
-cudaError_t launch_step(const float* src, float* dst, const StepParams& P, int rows,
-                        unsigned* flag, cudaStream_t s);
+cudaError_t launch_step(const void* src, void* dst, const StepParams& P, int rows, unsigned* flag, cudaStream_t s);
 // Fields of the state whose post-collision populations are in src.
-cudaError_t launch_fields(const float* src, const StepParams& P, int rows, FieldOut out,
-                          cudaStream_t s);
+cudaError_t launch_fields(const void* src, const StepParams& P, int rows, FieldOut out, cudaStream_t s);
 // Per-CTA FP64 partial diagnostics into partials[grid][kDiagSlots].
-cudaError_t launch_diag_partials(const float* src, const StepParams& P, int rows,
-                                 double* partials, cudaStream_t s);
-// Same, from pre-collision populations in the public layout float[2][9][ny][nx].
+cudaError_t launch_diag_partials(const void* src, const StepParams& P, int rows, double* partials, cudaStream_t s);
+// Same, from pre-collision FP32 populations in the public layout float[2][9][ny][nx].
 cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int rows,
                                      double* partials, cudaStream_t s);
 // Reduces nblocks partial rows into out[kDiagSlots] (one CTA).
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s);
+
+// 16-bit storage: FP32 post-collision planes float[18][ny][nx] <-> the
+// deviation layout of P.precision (see cmrt_step.cu).
+cudaError_t launch_encode(const float* post32, const StepParams& P, void* state, cudaStream_t s);
+cudaError_t launch_decode(const void* state, const StepParams& P, float* post32, cudaStream_t s);
 
 // Initial state: writes into post the populations P_{-1} whose streaming gives
 // the equilibrium state of Eq. equ_equ at t = 0.

@@ -2,18 +2,25 @@
 // as one row-marching kernel for sm_103a.
 //
 // Data layout in HBM: the state is the post-collision (pre-streaming)
-// populations P_{t-1} as 18 planes float[18][ny][nx] (red links 0..8, then
-// blue links 0..8).  One launch gathers the pre-collision populations
-// f(t) = stream(P_{t-1}) on the fly ("pull"), performs the whole per-node
-// update and writes P_t to the other buffer at the node itself, so every
-// HBM access is coalesced: 72 B read + 72 B written per node.
+// populations P_{t-1}.  With FP32 storage they are 18 planes
+// float[18][ny][nx] (red links 0..8, then blue links 0..8).  With 16-bit
+// storage (FP16 or BF16) a node keeps its two colour densities in FP32 and
+// nine 16-bit pairs of deviations d_{C,i} = C_i - rho_C psi^C_i from a
+// reference that scales with the node's own colour density: plane 0 is
+// float2[ny][nx] (rho'_R, rho'_B), planes 1..9 are 16-bit pairs (d_R,i, d_B,i).
+// The stored densities rho'_C = rho_C - sum_i round(d_C,i) absorb the
+// rounding, so a record decodes to populations summing to rho_C.
+// One launch gathers the pre-collision populations f(t) = stream(P_{t-1})
+// on the fly ("pull"), performs the whole per-node update and writes P_t to
+// the other buffer at the node itself, so every HBM access is coalesced:
+// 72 B (FP32) or 44 B (16-bit) read and as much written per node.
 //
 // A CTA of 128 threads owns a strip of 120 columns (plus 4 halo columns on
 // each side, 128 in all: one thread per column) and marches down a segment
-// of rows.  Rows of post-collision populations stream into an 8-row ring in
-// shared memory with 16-byte cp.async copies, two rows ahead of use.  Each
-// iteration runs a wavefront of four stages on consecutive rows, each stage
-// reading only what the previous one left in shared memory:
+// of rows.  Rows of the state stream into an 8-row ring in shared memory
+// with 16-byte cp.async copies, two rows ahead of use.  Each iteration runs
+// a wavefront of four stages on consecutive rows, each stage reading only
+// what the previous one left in shared memory:
 //   A (row s-1)  gather f, colour moments, rho^N, Phi'          (tile + 3)
 //   B (row s-2)  grad rho^N and n-hat with the compact stencil   (tile + 2)
 //   C (row s-3)  K = div n-hat, force G, force-adjusted u        (tile + 1)
@@ -27,27 +34,21 @@
 // small, so FP32 rounding stays at the level of population storage.  The
 // reconstruction M^{-1} dm is grouped by the parity of each column k^(p)
 // under c -> -c, which the k vectors of App. A have by construction.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "cmrt_device.cuh"
 
 namespace cmrt {
 namespace {
 
 constexpr int kPlanes = 18;
-constexpr int kPopFloats = kRing * kPlanes * kWin;
-// ring A: rho^N, Phi', rho, j_x, j_y over 8 rows
-constexpr int kAF = 5;
-constexpr int kAFloats = 8 * kAF * kWin;
 // ring B: grad rho^N (x, y), n-hat (x, y) over 4 rows
 constexpr int kBF = 4;
 constexpr int kBFloats = 4 * kBF * kWin;
 // ring C: G (x, y), u (x, y) over 4 rows
 constexpr int kCF = 4;
 constexpr int kCFloats = 4 * kCF * kWin;
-constexpr int kSmemFloats = kPopFloats + kAFloats + kBFloats + kCFloats;
-// 16-byte chunks of one ring row (18 planes x 128 columns) and chunks per thread
-constexpr int kChunksPerPlane = kWin / 4;
-constexpr int kRowChunks = kPlanes * kChunksPerPlane;
-constexpr int kChunkIters = (kRowChunks + kThreads - 1) / kThreads;
 
 // The reconstruction below relies on these symmetries of App. A's k vectors.
 static_assert(kinv(4, 3) == kinv(8, 3) && kinv(4, 4) == kinv(8, 4) && kinv(4, 6) == kinv(8, 6), "even x");
@@ -60,23 +61,13 @@ static_assert(kinv(1, 3) == kinv(1, 4) && kinv(1, 1) == kinv(1, 2) && kinv(1, 7)
 static_assert(kinv(8, 2) == 0.f && kinv(8, 5) == 0.f && kinv(8, 8) == 0.f && kinv(0, 1) == 0.f &&
               kinv(0, 5) == 0.f && kinv(0, 7) == 0.f, "zeros");
 
-struct Rings {
-    float* pop;
-    float* a;
-    float* b;
-    float* c;
-    __device__ __forceinline__ float* P(int row, int q) const {
-        return pop + (((row & (kRing - 1)) * kPlanes) + q) * kWin;
-    }
-    __device__ __forceinline__ float* A(int row, int f) const { return a + (((row & 7) * kAF) + f) * kWin; }
-    __device__ __forceinline__ float* B(int row, int f) const { return b + (((row & 3) * kBF) + f) * kWin; }
-    __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
-};
-
-__device__ __forceinline__ void cp_async16(unsigned smem_addr, const float* gmem) {
+__device__ __forceinline__ void cp_async16(unsigned smem_addr, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async4(unsigned smem_addr, const float* gmem) {
+__device__ __forceinline__ void cp_async8(unsigned smem_addr, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned smem_addr, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -92,75 +83,303 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 
-// Per-thread plan of the asynchronous row copies: which 16-byte chunks of a
-// ring row this thread fetches, as (shared offset, global offset) pairs that
-// are the same for every row of the strip.
-template <bool VEC>
-struct CopyPlan {
-    static constexpr int kN = VEC ? kChunkIters : kPlanes;
-    unsigned soff[kN];  // byte offset inside a ring row
-    size_t goff[kN];    // element offset inside a global row (plane * nx * ny + column)
-    int n;
+__device__ __forceinline__ float sum9(const float (&v)[9]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
 
-    __device__ __forceinline__ void init(int x0, int nx, size_t plane) {
-        n = 0;
-        if (VEC) {
+// Segregation term of link i, w_i (s . c-hat_i) for a vector s (Eq. eq_re_color
+// with phi_i = w_i phim folded into s).
+__device__ __forceinline__ void segregation(float sx, float sy, float (&seg)[9]) {
+    seg[0] = 0.0f;
+    seg[8] = lw(8) * sx;
+    seg[4] = -seg[8];
+    seg[2] = lw(2) * sy;
+    seg[6] = -seg[2];
+    const float d1 = lw(1) * chx(1) * (sx + sy);
+    const float d3 = lw(3) * chx(1) * (sy - sx);
+    seg[1] = d1;
+    seg[5] = -d1;
+    seg[3] = d3;
+    seg[7] = -d3;
+}
+
+// ---------------------------------------------------------------------------
+// Storage layouts.  A layout fixes the bytes of one ring row, how a thread
+// copies its share of a row from HBM, how stage A / D gather the 18
+// pre-collision populations of a node from the ring, and how stage D stores
+// the node's post-collision populations.
+// ---------------------------------------------------------------------------
+
+// 32-bit: 18 FP32 planes.
+struct LayoutF32 {
+    static constexpr int kSlotBytes = kPlanes * kWin * 4;
+    static constexpr bool kSplitA = false;  // ring A keeps rho^N for stage D
+    static constexpr int kChunks = kSlotBytes / 16;
+    static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
+    static constexpr size_t node_bytes() { return kPlanes * 4; }
+
+    template <bool VEC>
+    struct Plan {
+        static constexpr int kN = VEC ? kVecIters : kPlanes;
+        unsigned soff[kN];  // byte offset inside a ring row
+        size_t goff[kN];    // byte offset inside the state, row 0
+        int n;
+        __device__ __forceinline__ void init(int x0, int nx, size_t nodes) {
+            n = 0;
+            if (VEC) {
+                constexpr int kPer = kWin / 4;
+#pragma unroll
+                for (int m = 0; m < kN; ++m) {
+                    const int c = threadIdx.x + m * kThreads;
+                    const int q = c / kPer;
+                    const int w4 = (c - q * kPer) * 4;
+                    soff[m] = static_cast<unsigned>((q * kWin + w4) * 4);
+                    goff[m] = (static_cast<size_t>(q) * nodes + wrap(x0 - kHalo + w4, nx)) * 4;
+                    if (c < kChunks) n = m + 1;
+                }
+            } else {
+                const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
+#pragma unroll
+                for (int q = 0; q < kN; ++q) {
+                    soff[q] = static_cast<unsigned>((q * kWin + threadIdx.x) * 4);
+                    goff[q] = (static_cast<size_t>(q) * nodes + gx) * 4;
+                }
+                n = kN;
+            }
+        }
+        __device__ __forceinline__ void issue(unsigned slot_addr, const char* state, int gy, int nx) const {
+            const char* row = state + static_cast<size_t>(gy) * nx * 4;
 #pragma unroll
             for (int m = 0; m < kN; ++m) {
-                const int c = threadIdx.x + m * kThreads;
-                const int q = c / kChunksPerPlane;
-                const int w4 = (c - q * kChunksPerPlane) * 4;
-                soff[m] = static_cast<unsigned>((q * kWin + w4) * sizeof(float));
-                goff[m] = static_cast<size_t>(q) * plane + wrap(x0 - kHalo + w4, nx);
-                if (c < kRowChunks) n = m + 1;
+                if (m < n) {
+                    if (VEC) cp_async16(slot_addr + soff[m], row + goff[m]);
+                    else cp_async4(slot_addr + soff[m], row + goff[m]);
+                }
             }
-        } else {
-            const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
-#pragma unroll
-            for (int q = 0; q < kN; ++q) {
-                soff[q] = static_cast<unsigned>((q * kWin + threadIdx.x) * sizeof(float));
-                goff[q] = static_cast<size_t>(q) * plane + gx;
-            }
-            n = kN;
         }
+    };
+
+    __device__ __forceinline__ static const float* plane(const char* slot, int q) {
+        return reinterpret_cast<const float*>(slot) + q * kWin;
+    }
+    // populations (red, blue) of link i of the node in column `col` of a ring row
+    __device__ __forceinline__ static void pair(const char* slot, int i, int col, const StepParams&, float& r,
+                                                float& b) {
+        r = plane(slot, i)[col];
+        b = plane(slot, 9 + i)[col];
     }
 
-    __device__ __forceinline__ void issue(unsigned ring_row_addr, const float* grow) const {
+    // Store of the post-collision populations of one node.  The minority colour
+    // is formed directly and the majority as the rest of f+, so that
+    // R++ + B++ = f+ holds to one rounding of the majority.  (sx, sy) is the
+    // red segregation vector beta phi rho_R rho_B / rho e of Eq. eq_re_color.
+    __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
+                                                 float rr, float rb, float inv_rho, float sx, float sy,
+                                                 const StepParams&) {
+        float* out = reinterpret_cast<float*>(dst) + node;
+        const bool red_major = rr >= rb;
+        const float amin = (red_major ? rb : rr) * inv_rho;
+        const float smin = red_major ? -1.0f : 1.0f;  // minority's sign of the segregation term
+        float seg[9];
+        segregation(smin * sx, smin * sy, seg);
+        float* out_min = out + (red_major ? 9 * nodes : 0);
+        float* out_maj = out + (red_major ? 0 : 9 * nodes);
 #pragma unroll
-        for (int m = 0; m < kN; ++m) {
-            if (m < n) {
-                if (VEC) cp_async16(ring_row_addr + soff[m], grow + goff[m]);
-                else cp_async4(ring_row_addr + soff[m], grow + goff[m]);
-            }
+        for (int i = 0; i < 9; ++i) {
+            const float cmin = fmaf(amin, fp[i], seg[i]);
+            __stcs(out_min + i * nodes, cmin);
+            __stcs(out_maj + i * nodes, fp[i] - cmin);
         }
     }
+};
+
+// 16-bit deviations (H = __half2 or __nv_bfloat162) from rho_C psi^C_i.
+template <class H>
+struct Layout16 {
+    static constexpr int kRhoBytes = kWin * 8;  // float2 (rho_R, rho_B) per column
+    static constexpr int kDevBytes = kWin * 4;  // one 16-bit pair per column and link
+    static constexpr int kSlotBytes = kRhoBytes + 9 * kDevBytes;
+    static constexpr bool kSplitA = true;  // smaller ring A, stage D recomputes rho^N
+    static constexpr int kChunks = kSlotBytes / 16;
+    static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
+    static constexpr size_t node_bytes() { return 8 + 9 * 4; }
+
+    __device__ __forceinline__ static float2 to2(H v);
+    __device__ __forceinline__ static H from2(float a, float b);
+
+    template <bool VEC>
+    struct Plan {
+        static constexpr int kN = VEC ? kVecIters : 10;
+        unsigned soff[kN];
+        size_t goff[kN];     // byte offset of the chunk in row 0 of its plane
+        unsigned shift[kN];  // log2 of the element size of its plane
+        int n;
+        __device__ __forceinline__ void init(int x0, int nx, size_t nodes) {
+            n = 0;
+            if (VEC) {
+                constexpr int kRhoChunks = kRhoBytes / 16;  // 2 columns each
+                constexpr int kDevChunks = kDevBytes / 16;  // 4 columns each
+#pragma unroll
+                for (int m = 0; m < kN; ++m) {
+                    const int c = threadIdx.x + m * kThreads;
+                    if (c < kRhoChunks) {
+                        soff[m] = static_cast<unsigned>(c * 16);
+                        goff[m] = static_cast<size_t>(wrap(x0 - kHalo + 2 * c, nx)) * 8;
+                        shift[m] = 3;
+                    } else {
+                        const int k = c - kRhoChunks;
+                        const int p = k / kDevChunks;
+                        const int w4 = (k - p * kDevChunks) * 4;
+                        soff[m] = static_cast<unsigned>(kRhoBytes + p * kDevBytes + w4 * 4);
+                        goff[m] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 +
+                                  static_cast<size_t>(wrap(x0 - kHalo + w4, nx)) * 4;
+                        shift[m] = 2;
+                    }
+                    if (c < kChunks) n = m + 1;
+                }
+            } else {
+                const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
+                soff[0] = threadIdx.x * 8;
+                goff[0] = static_cast<size_t>(gx) * 8;
+                shift[0] = 3;
+#pragma unroll
+                for (int p = 0; p < 9; ++p) {
+                    soff[1 + p] = static_cast<unsigned>(kRhoBytes + p * kDevBytes + threadIdx.x * 4);
+                    goff[1 + p] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 + static_cast<size_t>(gx) * 4;
+                    shift[1 + p] = 2;
+                }
+                n = kN;
+            }
+        }
+        __device__ __forceinline__ void issue(unsigned slot_addr, const char* state, int gy, int nx) const {
+            const size_t row_nodes = static_cast<size_t>(gy) * nx;
+#pragma unroll
+            for (int m = 0; m < kN; ++m) {
+                if (m < n) {
+                    const char* g = state + goff[m] + (row_nodes << shift[m]);
+                    if (VEC) cp_async16(slot_addr + soff[m], g);
+                    else if (m == 0) cp_async8(slot_addr + soff[m], g);
+                    else cp_async4(slot_addr + soff[m], g);
+                }
+            }
+        }
+    };
+
+    // reference weight psi^C_i of link i: rest, axis or diagonal class
+    __device__ __forceinline__ static float psi_r(int i, const StepParams& P) {
+        return i == 0 ? P.psi_r[0] : ((i & 1) ? P.psi_r[2] : P.psi_r[1]);
+    }
+    __device__ __forceinline__ static float psi_b(int i, const StepParams& P) {
+        return i == 0 ? P.psi_b[0] : ((i & 1) ? P.psi_b[2] : P.psi_b[1]);
+    }
+    __device__ __forceinline__ static void pair(const char* slot, int i, int col, const StepParams& P, float& r,
+                                                float& b) {
+        const float2 rho = reinterpret_cast<const float2*>(slot)[col];
+        const H d = reinterpret_cast<const H*>(slot + kRhoBytes + i * kDevBytes)[col];
+        const float2 dv = to2(d);
+        r = fmaf(rho.x, psi_r(i, P), dv.x);
+        b = fmaf(rho.y, psi_b(i, P), dv.y);
+    }
+
+    __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
+                                                 float rr, float rb, float inv_rho, float sx, float sy,
+                                                 const StepParams& P) {
+        float seg[9];
+        segregation(sx, sy, seg);
+        H* dev = reinterpret_cast<H*>(dst + nodes * 8) + node;
+        const float aR = rr * inv_rho, aB = rb * inv_rho;
+        // the stored densities absorb the rounding of the deviations, so that the
+        // decoded populations of the record sum to rho_R and rho_B (colour mass is
+        // conserved as with FP32 storage): rho'_C = rho_C - sum_i round(d_C,i)
+        float er = 0.0f, eb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float R = fmaf(aR, fp[i], seg[i]);
+            const float B = fmaf(aB, fp[i], -seg[i]);
+            const H h = from2(fmaf(-rr, psi_r(i, P), R), fmaf(-rb, psi_b(i, P), B));
+            const float2 back = to2(h);
+            er += back.x;
+            eb += back.y;
+            dev[i * nodes] = h;
+        }
+        reinterpret_cast<float2*>(dst)[node] = make_float2(rr - er, rb - eb);
+    }
+};
+
+template <>
+__device__ __forceinline__ float2 Layout16<__half2>::to2(__half2 v) { return __half22float2(v); }
+template <>
+__device__ __forceinline__ __half2 Layout16<__half2>::from2(float a, float b) { return __floats2half2_rn(a, b); }
+template <>
+__device__ __forceinline__ float2 Layout16<__nv_bfloat162>::to2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat162 Layout16<__nv_bfloat162>::from2(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+
+using LayoutF16 = Layout16<__half2>;
+using LayoutB16 = Layout16<__nv_bfloat162>;
+
+// ---------------------------------------------------------------------------
+// Shared-memory rings of one CTA.
+// ---------------------------------------------------------------------------
+template <class L>
+struct Geometry {
+    static constexpr int kPopBytes = kRing * L::kSlotBytes;
+    // ring A: without kSplitA, rho^N, Phi', rho, j_x, j_y over 8 rows; with it,
+    // Phi' over 8 rows (ring Q) and rho^N, rho, j_x, j_y over 4 rows
+    static constexpr int kQFloats = L::kSplitA ? 8 * kWin : 0;
+    static constexpr int kAFloats = L::kSplitA ? 4 * 4 * kWin : 8 * 5 * kWin;
+    static constexpr int kBytes = kPopBytes + 4 * (kQFloats + kAFloats + kBFloats + kCFloats);
+};
+
+template <class L>
+struct Rings {
+    char* pop;
+    float* q;
+    float* a;
+    float* b;
+    float* c;
+    __device__ __forceinline__ const char* slot(int row) const { return pop + (row & (kRing - 1)) * L::kSlotBytes; }
+    // ring A fields
+    __device__ __forceinline__ float* rhoN(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 4 + 0) * kWin : a + ((row & 7) * 5 + 0) * kWin;
+    }
+    __device__ __forceinline__ float* phip(int row) const {
+        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 5 + 1) * kWin;
+    }
+    __device__ __forceinline__ float* rho(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 4 + 1) * kWin : a + ((row & 7) * 5 + 2) * kWin;
+    }
+    __device__ __forceinline__ float* jx(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 4 + 2) * kWin : a + ((row & 7) * 5 + 3) * kWin;
+    }
+    __device__ __forceinline__ float* jy(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 4 + 3) * kWin : a + ((row & 7) * 5 + 4) * kWin;
+    }
+    __device__ __forceinline__ float* B(int row, int f) const { return b + (((row & 3) * kBF) + f) * kWin; }
+    __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
 };
 
 // Pre-collision populations at (row y, window column t): pull from the
 // post-collision ring, f_i(r) = P_i(r - c_i) (Eq. equ_evolution), with
 // half-way bounce-back P_opp(i)(r) where r - c_i lies beyond a wall.
 // With PRE the rows hold pre-collision populations f(t) already in place
-// (the public layout), so the node's own column is read unshifted.
-template <bool WALLS, bool PRE = false>
-__device__ __forceinline__ void gather(const Rings& R, int y, int t, int ny, float (&fr)[9], float (&fb)[9]) {
+// (the public FP32 layout), so the node's own column is read unshifted.
+template <class L, bool WALLS, bool PRE>
+__device__ __forceinline__ void gather(const Rings<L>& R, int y, int t, int ny, const StepParams& P,
+                                       float (&fr)[9], float (&fb)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sy = y - lcy(i);
         if (PRE) {
-            fr[i] = R.P(y, i)[t];
-            fb[i] = R.P(y, 9 + i)[t];
+            L::pair(R.slot(y), i, t, P, fr[i], fb[i]);
         } else if (WALLS && (sy < 0 || sy >= ny)) {
-            fr[i] = R.P(y, lopp(i))[t];
-            fb[i] = R.P(y, 9 + lopp(i))[t];
+            L::pair(R.slot(y), lopp(i), t, P, fr[i], fb[i]);
         } else {
-            fr[i] = R.P(sy, i)[t - lcx(i)];
-            fb[i] = R.P(sy, 9 + i)[t - lcx(i)];
+            L::pair(R.slot(sy), i, t - lcx(i), P, fr[i], fb[i]);
         }
     }
-}
-
-__device__ __forceinline__ float sum9(const float (&v)[9]) {
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
 }
 
 // Compact derivatives of a ring field around (row y, column t).
@@ -178,34 +397,37 @@ __device__ __forceinline__ float ddy_at(Row rowp, int y, int t) {
     return ddy(n[t], s[t], n[t + 1], n[t - 1], s[t + 1], s[t - 1]);
 }
 
-template <bool VEC, bool WALLS, Pass MODE, bool PRE = false>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_chain(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, const int rows,
-            FieldOut fo, unsigned* __restrict__ flag, double* __restrict__ partials) {
-    extern __shared__ __align__(16) float smem[];
-    Rings R{smem, smem + kPopFloats, smem + kPopFloats + kAFloats, smem + kPopFloats + kAFloats + kBFloats};
-    const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+template <class L>
+constexpr int min_ctas_per_sm() {
+    return Geometry<L>::kBytes + 1024 <= 228 * 1024 / 3 ? 3 : 2;
+}
 
+// Diagnostics accumulators of one thread (Pass::Diag).
+struct DiagAcc {
+    double r = 0.0, b = 0.0, jx = 0.0, jy = 0.0, u2 = 0.0, bad = 0.0;
+};
+
+// One tile: the strip [x0, x0 + 120) of rows [y0, y0 + rows) of a lattice,
+// with its whole four-stage row pipeline.  Leaves no copy in flight.
+template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
+__device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop_addr, const char* __restrict__ src,
+                                           char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
+                                           const int rows, const FieldOut& fo, unsigned* __restrict__ flag,
+                                           DiagAcc& acc) {
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny;
-    const size_t plane = static_cast<size_t>(nx) * ny;
-    const int x0 = blockIdx.x * kTileX;
-    const int y0 = blockIdx.y * rows;
+    const size_t nodes = static_cast<size_t>(nx) * ny;
     const int y_end = min(y0 + rows, ny);
     const int s_first = y0 - 4;
     const int s_last = y_end + 3;
     const int iters = (y_end - y0) + 8;
     auto row_ok = [&](int r) { return !WALLS || (r >= 0 && r < ny); };
 
-    CopyPlan<VEC> plan;
-    plan.init(x0, nx, plane);
+    typename L::template Plan<VEC> plan;
+    plan.init(x0, nx, nodes);
     auto issue_row = [&](int row) {
-        const unsigned ring_row = pop_addr + static_cast<unsigned>((row & (kRing - 1)) * kPlanes * kWin * 4);
-        plan.issue(ring_row, src + static_cast<size_t>(wrap(row, ny)) * nx);
+        plan.issue(pop_addr + static_cast<unsigned>((row & (kRing - 1)) * L::kSlotBytes), src, wrap(row, ny), nx);
     };
-
-    // diagnostics accumulators (Pass::Diag)
-    double acc_r = 0.0, acc_b = 0.0, acc_jx = 0.0, acc_jy = 0.0, acc_u2 = 0.0, acc_bad = 0.0;
 
     if (row_ok(s_first)) issue_row(s_first);
     cp_commit();
@@ -224,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int ya = s - 1;
             if (ya >= y0 - 3 && ya <= y_end + 2 && row_ok(ya) && t >= 1 && t < kWin - 1) {
                 float fr[9], fb[9];
-                gather<WALLS, PRE>(R, ya, t, ny, fr, fb);
+                gather<L, WALLS, PRE>(R, ya, t, ny, P, fr, fb);
                 const float rr = sum9(fr);
                 const float rb = sum9(fb);
                 // colour-blind momentum sum_i f_i c_i (Eq. equ_u_def)
@@ -234,20 +456,20 @@ __global__ void __launch_bounds__(kThreads, 2)
                                  (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
                 const float a = rr * P.inv_rho0_r;
                 const float b = rb * P.inv_rho0_b;
-                const float rn = (a - b) * rcp(a + b);             // Eq. equ_rhoN_def
+                const float rn = (a - b) * rcp(a + b);                 // Eq. equ_rhoN_def
                 const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
-                R.A(ya, 0)[t] = rn;
-                R.A(ya, 1)[t] = phip;
-                R.A(ya, 2)[t] = rr + rb;
-                R.A(ya, 3)[t] = jx;
-                R.A(ya, 4)[t] = jy;
+                R.rhoN(ya)[t] = rn;
+                R.phip(ya)[t] = phip;
+                R.rho(ya)[t] = rr + rb;
+                R.jx(ya)[t] = jx;
+                R.jy(ya)[t] = jy;
                 if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
-                    R.A(-1, 0)[t] = rn;
-                    R.A(-1, 1)[t] = phip;
+                    R.rhoN(-1)[t] = rn;
+                    R.phip(-1)[t] = phip;
                 }
                 if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
-                    R.A(ny, 0)[t] = rn;
-                    R.A(ny, 1)[t] = phip;
+                    R.rhoN(ny)[t] = rn;
+                    R.phip(ny)[t] = phip;
                 }
             }
         }
@@ -257,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         {
             const int yb = s - 2;
             if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-                auto rn_row = [&](int r) { return R.A(r, 0); };
+                auto rn_row = [&](int r) { return R.rhoN(r); };
                 const float gx = ddx_at(rn_row, yb, t);
                 const float gy = ddy_at(rn_row, yb, t);
                 // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
@@ -294,15 +516,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
                 const float gx = R.B(yc, 0)[t];
                 const float gy = R.B(yc, 1)[t];
-                const float rho = R.A(yc, 2)[t];
+                const float rho = R.rho(yc)[t];
                 // G = sigma K grad rho^N / 2 + rho g_acc + g_vol (Eq. equ_stforce plus body force)
                 const float hk = P.half_sigma * K;
                 const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
                 const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
                 const float inv_rho = rcp(rho);
                 // force-adjusted velocity (Eq. equ_u_def)
-                const float ux = fmaf(0.5f, Gx, R.A(yc, 3)[t]) * inv_rho;
-                const float uy = fmaf(0.5f, Gy, R.A(yc, 4)[t]) * inv_rho;
+                const float ux = fmaf(0.5f, Gx, R.jx(yc)[t]) * inv_rho;
+                const float uy = fmaf(0.5f, Gy, R.jy(yc)[t]) * inv_rho;
                 R.C(yc, 0)[t] = Gx;
                 R.C(yc, 1)[t] = Gy;
                 R.C(yc, 2)[t] = ux;
@@ -325,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int gxo = x0 + t - kHalo;
             if (yd >= y0 && yd < y_end && t >= kHalo && t < kWin - kHalo && gxo < nx) {
                 float fr[9], fb[9], f[9];
-                gather<WALLS, PRE>(R, yd, t, ny, fr, fb);
+                gather<L, WALLS, PRE>(R, yd, t, ny, P, fr, fb);
                 const float rr = sum9(fr);
                 const float rb = sum9(fb);
 #pragma unroll
@@ -337,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (!isfinite(rho)) atomicOr(flag, 1u);
                     const float Gx = R.C(yd, 0)[t];
                     const float Gy = R.C(yd, 1)[t];
-                    auto phip_row = [&](int r) { return R.A(r, 1); };
+                    auto phip_row = [&](int r) { return R.phip(r); };
                     const float dPx = ddx_at(phip_row, yd, t);
                     const float dPy = ddy_at(phip_row, yd, t);
                     const float divu = ddx_at([&](int r) { return R.C(r, 2); }, yd, t) +
@@ -346,7 +568,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                     // local shear eigenvalue (Sec. 2: nu(rho^N) = (2/lambda_3 - 1)/6)
                     float nu;
                     if (P.visc_mode == 0) {
-                        const float rn = R.A(yd, 0)[t];
+                        float rn;
+                        if (L::kSplitA) {
+                            // rho^N of this node (Eq. equ_rhoN_def); the 4-row ring A may
+                            // already hold a wall's ghost row in row yd's slot
+                            const float ra = rr * P.inv_rho0_r, ba = rb * P.inv_rho0_b;
+                            rn = (ra - ba) * rcp(ra + ba);
+                        } else {
+                            rn = R.rhoN(yd)[t];
+                        }
                         nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
                     } else {
                         nu = P.eta * inv_rho;
@@ -400,40 +630,16 @@ __global__ void __launch_bounds__(kThreads, 2)
                     df[5] = pe - q1;  // (-1, -1)
                     df[7] = me + q2;  // (+1, -1)
                     df[3] = me - q2;  // (-1, +1)
+                    float fp[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fp[i] = f[i] + df[i];  // f+ = f + M^{-1} dm
                     // recolour (Eq. eq_re_color): red moves along e = grad rho^N / |grad rho^N| = -n-hat,
                     // by beta phi_i rho_R rho_B / rho (e . c-hat_i); phi_i = w_i phim for i != 0
                     const float ex = -R.B(yd, 2)[t];
                     const float ey = -R.B(yd, 3)[t];
                     const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
-                    const float seg = P.beta * (rr * rb) * inv_rho * phim;
-                    // the minority colour is formed directly and the majority as the rest
-                    // of f+, so that R++ + B++ = f+ holds to one rounding of the majority
-                    const bool red_major = rr >= rb;
-                    const float amin = (red_major ? rb : rr) * inv_rho;
-                    const float smin = red_major ? -seg : seg;  // minority's sign of the segregation term
-                    const float sx = smin * ex, sy = smin * ey;
-                    float dmin[9];
-                    dmin[0] = 0.0f;
-                    dmin[8] = lw(8) * sx;
-                    dmin[4] = -dmin[8];
-                    dmin[2] = lw(2) * sy;
-                    dmin[6] = -dmin[2];
-                    const float dd1 = lw(1) * chx(1) * (sx + sy);
-                    const float dd3 = lw(3) * chx(1) * (sy - sx);
-                    dmin[1] = dd1;
-                    dmin[5] = -dd1;
-                    dmin[3] = dd3;
-                    dmin[7] = -dd3;
-                    const size_t o = static_cast<size_t>(yd) * nx + gxo;
-                    float* out_min = dst + o + (red_major ? 9 * plane : 0);
-                    float* out_maj = dst + o + (red_major ? 0 : 9 * plane);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const float fp = f[i] + df[i];  // f+ = f + M^{-1} dm
-                        const float cmin = fmaf(amin, fp, dmin[i]);
-                        __stcs(out_min + i * plane, cmin);
-                        __stcs(out_maj + i * plane, fp - cmin);
-                    }
+                    const float sg = P.beta * (rr * rb) * inv_rho * phim;
+                    L::store(dst, nodes, static_cast<size_t>(yd) * nx + gxo, fp, rr, rb, inv_rho, sg * ex, sg * ey, P);
                 } else if (MODE == Pass::Fields) {
                     const size_t o = static_cast<size_t>(yd) * nx + gxo;
                     if (fo.rho_r) fo.rho_r[o] = rr;
@@ -445,23 +651,43 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const float jx = (f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]);
                     const float jy = (f[1] + f[2] + f[3]) - (f[5] + f[6] + f[7]);
                     if (isfinite(rho)) {
-                        acc_r += rr;
-                        acc_b += rb;
-                        acc_jx += jx;
-                        acc_jy += jy;
-                        acc_u2 = fmax(acc_u2, static_cast<double>(ux) * ux + static_cast<double>(uy) * uy);
+                        acc.r += rr;
+                        acc.b += rb;
+                        acc.jx += jx;
+                        acc.jy += jy;
+                        acc.u2 = fmax(acc.u2, static_cast<double>(ux) * ux + static_cast<double>(uy) * uy);
                     } else {
-                        acc_bad += 1.0;
+                        acc.bad += 1.0;
                     }
                 }
             }
         }
     }
     cp_wait<0>();
+}
+
+template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
+__global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>())
+    k_chain(const char* __restrict__ src, char* __restrict__ dst, const StepParams P, const int rows, FieldOut fo,
+            unsigned* __restrict__ flag, double* __restrict__ partials) {
+    using G = Geometry<L>;
+    extern __shared__ __align__(16) char smem[];
+    Rings<L> R;
+    R.pop = smem;
+    R.q = reinterpret_cast<float*>(smem + G::kPopBytes);
+    R.a = R.q + G::kQFloats;
+    R.b = R.a + G::kAFloats;
+    R.c = R.b + kBFloats;
+    const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+
+    DiagAcc acc;
+    chain_tile<L, VEC, WALLS, MODE, PRE>(R, pop_addr, src, dst, P, static_cast<int>(blockIdx.x) * kTileX,
+                                         static_cast<int>(blockIdx.y) * rows, rows, fo, flag, acc);
+    const int t = threadIdx.x;
 
     if (MODE == Pass::Diag) {
         // warp shuffle reduction, then across the CTA's warps in shared memory
-        double v[kDiagSlots] = {acc_r, acc_b, acc_jx, acc_jy, acc_u2, acc_bad};
+        double v[kDiagSlots] = {acc.r, acc.b, acc.jx, acc.jy, acc.u2, acc.bad};
 #pragma unroll
         for (int j = 0; j < kDiagSlots; ++j) {
 #pragma unroll
@@ -523,52 +749,64 @@ __global__ void k_diag_reduce(const double* __restrict__ partials, int nblocks, 
     }
 }
 
-template <bool VEC, bool WALLS, Pass MODE, bool PRE = false>
-cudaError_t launch_one(const float* src, float* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
+template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
+cudaError_t launch_one(const void* src, void* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
                        double* partials, cudaStream_t s) {
     // the shared-memory opt-in is per kernel and per device: set it once for each
     static unsigned long long configured = 0;
-    const size_t smem = chain_smem_bytes();
+    const int smem = Geometry<L>::kBytes;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(k_chain<VEC, WALLS, MODE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
+        e = cudaFuncSetAttribute(k_chain<L, VEC, WALLS, MODE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    k_chain<VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(src, dst, P, rows, fo, flag,
-                                                                                    partials);
+    k_chain<L, VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(
+        static_cast<const char*>(src), static_cast<char*>(dst), P, rows, fo, flag, partials);
     return cudaGetLastError();
 }
 
-template <Pass MODE>
-cudaError_t launch_chain(const float* src, float* dst, const StepParams& P, int rows, FieldOut fo,
-                         unsigned* flag, double* partials, cudaStream_t s) {
+template <class L, Pass MODE, bool PRE = false>
+cudaError_t launch_layout(const void* src, void* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
+                          double* partials, cudaStream_t s) {
     const bool vec = (P.nx % 4) == 0;
     const bool walls = P.wall_y != 0;
-    if (vec && walls) return launch_one<true, true, MODE>(src, dst, P, rows, fo, flag, partials, s);
-    if (vec) return launch_one<true, false, MODE>(src, dst, P, rows, fo, flag, partials, s);
-    if (walls) return launch_one<false, true, MODE>(src, dst, P, rows, fo, flag, partials, s);
-    return launch_one<false, false, MODE>(src, dst, P, rows, fo, flag, partials, s);
+    if (vec && walls) return launch_one<L, true, true, MODE, PRE>(src, dst, P, rows, fo, flag, partials, s);
+    if (vec) return launch_one<L, true, false, MODE, PRE>(src, dst, P, rows, fo, flag, partials, s);
+    if (walls) return launch_one<L, false, true, MODE, PRE>(src, dst, P, rows, fo, flag, partials, s);
+    return launch_one<L, false, false, MODE, PRE>(src, dst, P, rows, fo, flag, partials, s);
+}
+
+template <Pass MODE>
+cudaError_t launch_chain(const void* src, void* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
+                         double* partials, cudaStream_t s) {
+    switch (P.precision) {
+        case kPrecF16: return launch_layout<LayoutF16, MODE>(src, dst, P, rows, fo, flag, partials, s);
+        case kPrecB16: return launch_layout<LayoutB16, MODE>(src, dst, P, rows, fo, flag, partials, s);
+        default: return launch_layout<LayoutF32, MODE>(src, dst, P, rows, fo, flag, partials, s);
+    }
 }
 
 }  // namespace
 
-size_t chain_smem_bytes() { return sizeof(float) * static_cast<size_t>(kSmemFloats); }
+size_t state_node_bytes(int precision) {
+    return precision == kPrecF32 ? LayoutF32::node_bytes() : LayoutF16::node_bytes();
+}
 
 dim3 chain_grid(int nx, int ny, int rows) {
     return dim3(static_cast<unsigned>((nx + kTileX - 1) / kTileX), static_cast<unsigned>((ny + rows - 1) / rows), 1);
 }
 
-int chain_rows(int nx, int ny, int sms) {
+int chain_rows(int nx, int ny, int sms, int precision) {
     // Rows per CTA: each CTA spends (rows + 8) row-iterations (8 fill the
-    // pipeline), and the CTAs run in waves of (SMs x 2 resident CTAs); pick
+    // pipeline), and the CTAs run in waves of (SMs x resident CTAs); pick
     // the segment length that minimises waves x (rows + 8).
     const int strips = (nx + kTileX - 1) / kTileX;
-    const long slots = 2L * (sms > 0 ? sms : 1);
+    const int per_sm = precision == kPrecF32 ? min_ctas_per_sm<LayoutF32>() : min_ctas_per_sm<LayoutF16>();
+    const long slots = static_cast<long>(per_sm) * (sms > 0 ? sms : 1);
     int best = 8;
     long best_cost = -1;
     for (int rows = 8; rows <= 512; rows += 8) {
@@ -584,29 +822,21 @@ int chain_rows(int nx, int ny, int sms) {
     return best;
 }
 
-cudaError_t launch_step(const float* src, float* dst, const StepParams& P, int rows, unsigned* flag,
-                        cudaStream_t s) {
+cudaError_t launch_step(const void* src, void* dst, const StepParams& P, int rows, unsigned* flag, cudaStream_t s) {
     return launch_chain<Pass::Step>(src, dst, P, rows, FieldOut{}, flag, nullptr, s);
 }
 
-cudaError_t launch_fields(const float* src, const StepParams& P, int rows, FieldOut out, cudaStream_t s) {
+cudaError_t launch_fields(const void* src, const StepParams& P, int rows, FieldOut out, cudaStream_t s) {
     return launch_chain<Pass::Fields>(src, nullptr, P, rows, out, nullptr, nullptr, s);
 }
 
-cudaError_t launch_diag_partials(const float* src, const StepParams& P, int rows, double* partials,
-                                 cudaStream_t s) {
+cudaError_t launch_diag_partials(const void* src, const StepParams& P, int rows, double* partials, cudaStream_t s) {
     return launch_chain<Pass::Diag>(src, nullptr, P, rows, FieldOut{}, nullptr, partials, s);
 }
 
 cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int rows, double* partials,
                                      cudaStream_t s) {
-    const bool vec = (P.nx % 4) == 0;
-    const bool walls = P.wall_y != 0;
-    const FieldOut none{};
-    if (vec && walls) return launch_one<true, true, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
-    if (vec) return launch_one<true, false, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
-    if (walls) return launch_one<false, true, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
-    return launch_one<false, false, Pass::Diag, true>(pre, nullptr, P, rows, none, nullptr, partials, s);
+    return launch_layout<LayoutF32, Pass::Diag, true>(pre, nullptr, P, rows, FieldOut{}, nullptr, partials, s);
 }
 
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s) {

@@ -136,3 +136,25 @@ def random_state_fields(nx, ny, seed, amplitude=0.05):
     rn = 0.5 * rn + 0.125 * (np.roll(rn, 1, 0) + np.roll(rn, -1, 0) + np.roll(rn, 1, 1) + np.roll(rn, -1, 1))
     u = rng.uniform(-amplitude, amplitude, size=(2, ny, nx))
     return rn, u
+
+
+def buoyant_drops(nx=16384, ny=8192, ndrops=256, seed=4, rmin=10.0, rmax=40.0, g=1e-6, Lambda=10.0):
+    """Light drops rising in a heavy ambient between walls at y = -1/2 and ny - 1/2.
+
+    Heavy (red, rho0 = 1) ambient, light (blue, rho0 = 1/Lambda) drops with
+    centres uniform in the box (kept clear of the walls by their radius) and
+    radii uniform in [rmin, rmax], gravity g along -y.  Smaller boxes keep the
+    drop count per unit area (replicas of the same seeded field)."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(rmin, rmax, ndrops)
+    cx = rng.uniform(0.0, nx, ndrops)
+    cy = rng.uniform(0.0, 1.0, ndrops) * (ny - 2 * r - 4) + r + 2
+    p = base_params(nx, ny, rho0_r=1.0, rho0_b=1.0 / Lambda, wall_y=True, g_acc=(0.0, -g))
+    blue = drops_field(nx, ny, list(zip(cx, cy)), list(r), periodic_y=False)
+    return p, -blue, np.zeros((2, ny, nx))
+
+
+def buoyant_replica(side=512, seed=4, **kw):
+    """Same generator on a side x side box with the drop count scaled by area."""
+    ndrops = max(1, int(round(256 * side * side / (16384 * 8192))))
+    return buoyant_drops(nx=side, ny=side, ndrops=ndrops, seed=seed, **kw)

@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(cm):
 
 
 def test_abi_version_and_struct_size(cm):
-    assert cm.cmrt_abi_version() == 1
+    assert cm.cmrt_abi_version() == 2
     assert cm.load().cmrt_params_size() == ctypes.sizeof(cm.cmrt_params)
 
 
@@ -56,7 +56,8 @@ def test_defaults_are_valid(cm):
     ("lambda7", 0.0, "lambda6, lambda7"),
     ("sigma", -1.0, "sigma"),
     ("stencil_order", 6, "stencil_order"),
-    ("precision", 1, "precision"),
+    ("precision", 3, "precision"),
+    ("precision_reference", 2, "precision_reference"),
     ("visc_mode", 3, "visc_mode"),
     ("wall_y", 2, "wall_y"),
     ("rho0_b", 0.0, "rho0"),

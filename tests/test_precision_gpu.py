@@ -1,0 +1,140 @@
+"""16-bit population storage (BF16 / FP16 deviations from rho_C psi^C_i,
+FP32 arithmetic) against the FP64 oracle and the FP32 path.
+
+The bars are the accuracy this storage form reaches (relative field error, u
+normalised by max(|u_ref|, 0.01)), with margin: rounding a 16-bit deviation
+at an interface, where the mixture term rho_R rho_B (alpha_R - alpha_B)/rho
+of the colour populations is ~4e-3, costs ~1e-6 per population per step, so
+FP16 stays within 1e-2 over 100 steps and BF16 (8-bit mantissa) within 1e-1.
+The measured per-field errors are reported by bench.py.
+"""
+import numpy as np
+import pytest
+
+from oracle import cmrt_oracle as O
+from paper_2005_04642_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2005_04642_gb300 import cmrt as cm  # noqa: E402
+
+BF16, FP16 = 1, 2
+BAR = {FP16: 1e-2, BF16: 1e-1}
+BAR_LONG = {FP16: 3e-2, BF16: 3e-1}
+
+
+def _field_errs(lat, p, R, B):
+    g = {k: v.double().cpu().numpy() for k, v in lat.fields().items()}
+    f = O.fields(R, B, p)
+    out = {}
+    for k in ("rho_r", "rho_b"):
+        out[k] = np.abs(g[k] - f[k]).max() / np.abs(f[k]).max()
+    uref = max(np.abs(np.stack([f["ux"], f["uy"]])).max(), 0.01)
+    for k in ("ux", "uy"):
+        out[k] = np.abs(g[k] - f[k]).max() / uref
+    return out
+
+
+@pytest.mark.parametrize("prec", [FP16, BF16])
+@pytest.mark.parametrize("ref", [0, 1])
+def test_encode_decode_round_trip(prec, ref):
+    nx, ny = 72, 40
+    d = I.base_params(nx, ny, precision=prec, precision_reference=ref)
+    rn, u = I.random_state_fields(nx, ny, seed=3, amplitude=0.02)
+    p = O.Params(**{k: v for k, v in d.items() if k not in ("precision", "precision_reference")})
+    R, B = O.init_state(rn, u[0], u[1], p)
+    pops = np.stack([R, B]).astype(np.float32)
+    lat = cm.Lattice(d)
+    lat.set_populations(pops)
+    back = lat.populations().cpu().numpy()
+    lat.close()
+    eps = 2.0 ** -11 if prec == FP16 else 2.0 ** -8
+    # the error is a rounding of the deviation from rho_C psi_i, far below the population
+    assert np.abs(back - pops).max() <= 2 * eps * np.abs(pops).max()
+
+
+def _oracle_params(d):
+    return O.Params(**{k: v for k, v in d.items() if k not in ("precision", "precision_reference")})
+
+
+@pytest.mark.parametrize("prec", [FP16, BF16])
+def test_static_drop_100_steps(prec):
+    d, rn, u = I.static_drop()
+    p = _oracle_params(d)
+    R, B = O.run(*O.init_state(rn, u[0], u[1], p), p, 100)
+    lat = cm.Lattice(dict(d, precision=prec), rn, u)
+    m0 = lat.diagnostics()
+    lat.step(100)
+    errs = _field_errs(lat, p, R, B)
+    m1 = lat.diagnostics()
+    lat.close()
+    for k, v in errs.items():
+        assert v <= BAR[prec], (k, v)
+    # the stored densities absorb the deviations' rounding: colour mass drifts
+    # only at the FP32 level, as with FP32 storage
+    assert abs(m1["mass_r"] - m0["mass_r"]) / m0["mass_r"] <= 1e-6
+    assert abs(m1["mass_b"] - m0["mass_b"]) / m0["mass_b"] <= 1e-6
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [FP16, BF16])
+def test_buoyant_replica_2000_steps(prec):
+    d, rn, u = I.buoyant_replica(side=128)
+    p = _oracle_params(d)
+    R, B = O.run(*O.init_state(rn, u[0], u[1], p), p, 2000)
+    lat = cm.Lattice(dict(d, precision=prec), rn, u)
+    lat.step(2000)
+    errs = _field_errs(lat, p, R, B)
+    lat.close()
+    for k, v in errs.items():
+        assert v <= BAR_LONG[prec], (k, v)
+
+
+def test_fp16_close_to_fp32_on_full_size_field():
+    """The reduced-precision form tracks the (oracle-checked) FP32 path on the
+    16384 x 8192 buoyant field over 50 steps, within the FP16 bar."""
+    d, rn, u = I.buoyant_drops()
+    a = cm.Lattice(d, rn, u)
+    b = cm.Lattice(dict(d, precision=FP16), rn, u)
+    a.step(50)
+    b.step(50)
+    fa, fb = a.fields(), b.fields()
+    a.close()
+    b.close()
+    for k in ("rho_r", "rho_b"):
+        assert float((fa[k] - fb[k]).abs().max() / fa[k].abs().max()) <= 1e-2
+    uref = max(float(torch.stack([fa["ux"], fa["uy"]]).abs().max()), 0.01)
+    for k in ("ux", "uy"):
+        assert float((fa[k] - fb[k]).abs().max()) / uref <= 1e-2
+
+
+@pytest.mark.slow
+def test_accuracy_table_buoyant_replica():
+    """Per-field error of every storage form against the FP64 oracle on a
+    128 x 128 replica of the buoyant-drops field after 2000 steps (the oracle
+    cannot run the 512^2 x 10k replica within a test).  Written to
+    gpurun_out/precision_accuracy.json when that directory exists."""
+    import json
+    import os
+    d, rn, u = I.buoyant_replica(side=128)
+    p = _oracle_params(d)
+    R, B = O.run(*O.init_state(rn, u[0], u[1], p), p, 2000)
+    table = {}
+    for name, prec, ref in (("fp32", 0, 0), ("fp16", FP16, 0), ("bf16", BF16, 0), ("fp16_wref", FP16, 1),
+                            ("bf16_wref", BF16, 1)):
+        lat = cm.Lattice(dict(d, precision=prec, precision_reference=ref), rn, u)
+        lat.step(2000)
+        table[name] = _field_errs(lat, p, R, B)
+        lat.close()
+    assert max(table["fp32"].values()) <= 1e-3
+    assert max(table["fp16"].values()) <= BAR_LONG[FP16]
+    assert max(table["bf16"].values()) <= BAR_LONG[BF16]
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "precision_accuracy.json"), "w") as fh:
+            json.dump({"workload": "buoyant replica 128x128, 1 drop, walls, g = 1e-6, 2000 steps",
+                       "errors": table}, fh, indent=1)
