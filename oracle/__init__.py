@@ -12,6 +12,9 @@ Modules
 ``cmrt_oracle``  the per-time-step update (Sec. 2, Sec. 3, App. A, App. B)
 ``analytic``     reference solutions used as physics pins (App. C, App. D and
                  textbook single-phase flows)
+``cmrt_adjoint`` the discrete adjoint (reverse mode) of the step, the L2
+                 colour-field objective and its gradient with checkpointing;
+                 pinned by central finite differences of ``cmrt_oracle``
 
 Every function cites the passage of the paper it follows.  Where the paper is
 silent, garbled or self-contradictory, the reading taken is stated in the
