@@ -351,7 +351,107 @@ def run_variants(args, cm, I, stream, fp32_ms):
                 "bytes_per_cell": nbytes, "achieved_GBs": nbytes * cells / (ms * 1e-3) / 1e9,
                 "frac_of_hbm_peak": nbytes * cells / (ms * 1e-3) / 1e9 / peak, "steps": steps,
                 "nonfinite": diag["nonfinite"]}
+        out.update(run_batch(cm, I, stream, steps, fp32_ms, peak))
+        out.update(run_adjoint(cm, I, stream))
     return out
+
+
+def run_adjoint(cm, I, stream):
+    """Cost of the discrete adjoint (cmrt_adjoint: forward with checkpoints,
+    segment recomputation, reverse sweep) against plain forward steps: the
+    256^2 drop of radius 32 (Lambda 10, gravity 1e-5 along -y) over 4000 steps
+    with checkpoints every 200, and a 2048^2 lattice of the same drops field
+    over 200 steps (checkpoints every 20) where launch latency no longer
+    dominates.  The objective's target is the final colour field of a run
+    with sigma 5 % larger."""
+    import torch
+    res = {}
+    for name, n, nsteps, K, drops in (("adjoint_256x256_drop_4000steps", 256, 4000, 200, 1),
+                                      ("adjoint_2048x2048_drops_200steps", 2048, 200, 20, 16)):
+        if drops == 1:
+            d = I.base_params(n, n, rho0_r=1.0, rho0_b=0.1, g_acc=(0.0, -1e-5))
+            rn0 = I.drops_field(n, n, [(n / 2.0, n / 2.0)], [32.0], dtype=np.float32)
+        else:
+            d, rn0, _ = I.random_drops(n, n, drops, 8.0, 64.0, 3, Lambda=10.0, g_acc=(0.0, -1e-5))
+            rn0 = rn0.astype(np.float32)
+        rn_dev = torch.from_numpy(rn0).cuda()
+        lt = cm.Lattice(dict(d, sigma=1.05 * d["sigma"]), rn_dev, None, stream=stream)
+        lt.step(nsteps)
+        f = lt.fields()
+        a, b = f["rho_r"] / d["rho0_r"], f["rho_b"] / d["rho0_b"]
+        target = ((a - b) / (a + b)).contiguous()
+        lt.close()
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), out
+
+        lat = cm.Lattice(d, rn_dev, None, stream=stream)
+        lat.step(10)  # warm-up
+        lat.close()
+        lat = cm.Lattice(d, rn_dev, None, stream=stream)
+        t_fwd, _ = timed(lambda: lat.step(nsteps))
+        lat.close()
+        lat = cm.Lattice(d, rn_dev, None, stream=stream)
+        l0 = lat.launches
+        t_adj, (J, g, _) = timed(lambda: lat.adjoint(nsteps, target, ckpt_every=K, want_rho_n0=True))
+        launches = lat.launches - l0
+        dev_bytes = cm.cmrt_device_bytes(lat.ctx)
+        lat.close()
+        torch.cuda.empty_cache()
+        res[name] = {"forward_ms_per_step": t_fwd / nsteps, "adjoint_ms_per_step": t_adj / nsteps,
+                     "adjoint_vs_forward": t_adj / t_fwd, "reverse_vs_forward": (t_adj - t_fwd) / t_fwd,
+                     "launches_per_step": launches / nsteps, "ckpt_every": K, "steps": nsteps,
+                     "device_bytes": dev_bytes, "J": J, "dJ_dsigma": g["sigma"]}
+    return res
+
+
+def run_batch(cm, I, stream, steps, fp32_ms, peak):
+    """The 512-lattice ensemble (sides 64..512, one drop each, sigma and
+    Lambda per member) in one persistent launch per step, replayed from CUDA
+    graphs: untuned rows (min(64, ny) per size class) against the autotuned
+    ones, each against the plain FP32 step of the 8192^2 lattice per cell."""
+    import torch
+    members = I.batch_ensemble(512, seed=5)
+    cells = sum(m[0]["nx"] * m[0]["ny"] for m in members)
+    b = cm.Batch(members, stream=stream)
+    graph = 32
+    steps = max(graph, (steps + graph - 1) // graph * graph)
+
+    def timed():
+        b.step(2 * graph)  # warm-up; records the graph of each parity
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches0 = b.launches
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, b.launches - launches0
+
+    ms_untuned, _ = timed()
+    tuned_us = b.tune()
+    ms, launches = timed()
+    diag = b.diagnostics()
+    sides = sorted({m[0]["nx"] for m in members})
+    single = N_SIDE * N_SIDE / (fp32_ms * 1e-3) / 1e6
+    value = cells / (ms * 1e-3) / 1e6
+    res = {"batch_512_lattices_sides64-512_fp32": {
+        "value": value, "unit": UNIT, "ms_per_step": ms, "members": len(members), "cells": cells,
+        "work_items_per_step": b.work_items, "launches_per_step": launches / steps, "graph_steps": graph,
+        "rows_per_class": {f"{s}x{s}": b.get_rows(s, s, 0) for s in sides},
+        "untuned_ms_per_step": ms_untuned, "tuner_speedup": ms_untuned / ms, "tuner_us_per_step": tuned_us,
+        "vs_fp32_single_lattice": value / single, "bytes_per_cell": 144,
+        "achieved_GBs": 144 * cells / (ms * 1e-3) / 1e9, "frac_of_hbm_peak": 144 * cells / (ms * 1e-3) / 1e9 / peak,
+        "steps": steps, "nonfinite": float(diag[:, 5].sum())}}
+    b.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():

@@ -49,9 +49,10 @@
 extern "C" {
 #endif
 
-#define CMRT_ABI_VERSION 2
+#define CMRT_ABI_VERSION 4
 
-typedef struct cmrt_ctx cmrt_ctx; /* opaque, owned by the library */
+typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
+typedef struct cmrt_batch cmrt_batch; /* opaque, owned by the library */
 
 typedef enum {
     CMRT_OK = 0,
@@ -190,6 +191,50 @@ size_t cmrt_device_bytes(const cmrt_ctx* c);
  * any stream capture.  Returns CMRT_ENONFINITE when out[5] > 0. */
 cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const float* pops, double out[6], void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Discrete adjoint (reverse mode) of the step, FP32 storage only.
+ *
+ * The step f(t+1) = S(f(t); theta) is the composition streaming o recolour
+ * o collision o (force, curvature, normal, gradients) o moments of Sec. 2 and
+ * App. A; its adjoint applies the transposed Jacobian of every one of those
+ * operations in reverse order (transposed gather with bounce-back,
+ * transposed MRT reconstruction and relaxation with the Jacobians of the
+ * equilibria, sources and correction tensor, adjoint recolour including the
+ * derivative of the unit normal and its eps-regularisation, the transposed
+ * compact stencils with their wall mirrors).  The paper has no adjoint: this
+ * is a library facility.  Parameters theta, in this order:
+ *   sigma, beta, lambda3_r, lambda3_b, g_acc[0], g_acc[1].
+ * Parameter gradients are accumulated in FP64, the adjoint fields in FP32.
+ * ------------------------------------------------------------------------ */
+
+/* Vector-Jacobian product of one step at the current state f(t) (the state
+ * is not advanced).
+ * lam_next: dJ/df(t+1), float[2][9][ny][nx] (pre-collision layout, host or
+ *           device).
+ * lam:      receives dJ/df(t) through this step, same layout.
+ * grad_params: NULL, or double[6] to which this step's dJ/dtheta is ADDED.
+ * Synchronises the stream.  CMRT_EINVAL for 16-bit storage. */
+cmrt_status cmrt_step_vjp(cmrt_ctx* c, const float* lam_next, float* lam, double grad_params[6]);
+
+/* Gradient of the colour-field mismatch after nsteps steps,
+ *   J = 1/2 sum_r (rho^N(r, t0 + nsteps) - target(r))^2,
+ * t0 the current time.  Runs the nsteps forward steps (the context ends at
+ * t0 + nsteps, as after cmrt_step), keeping a checkpoint every ckpt_every
+ * steps, then sweeps the segments backwards, recomputing each from its
+ * checkpoint.  Device memory: (ceil(nsteps/ckpt_every) + ckpt_every + 1)
+ * states of 72 B per node plus 38 scratch planes, kept for later calls.
+ * target:  float[ny][nx] (host or device).
+ * J:       NULL or receives J (FP64 sum).
+ * grad_params: NULL or receives dJ/dtheta (double[6]).
+ * grad_rho_n0: NULL or float[ny][nx] receiving dJ/drho^N_0, the gradient
+ *          with respect to the initial colour field given to cmrt_init (the
+ *          initial velocity held fixed); only at time 0 (else CMRT_EINVAL).
+ * Synchronises.  CMRT_EINVAL for 16-bit storage, nsteps < 1 or
+ * ckpt_every < 1, or on a batch member view; CMRT_ENONFINITE if the forward
+ * run produced a non-finite density. */
+cmrt_status cmrt_adjoint(cmrt_ctx* c, int64_t nsteps, int32_t ckpt_every, const float* target, double* J,
+                         double grad_params[6], float* grad_rho_n0);
+
 /* Frees the context and everything it allocated.  NULL is a no-op. */
 void cmrt_destroy(cmrt_ctx* c);
 
@@ -197,6 +242,102 @@ void cmrt_destroy(cmrt_ctx* c);
  * when c is NULL.  The string is owned by the library and stays valid until
  * the next call on the same context (or thread). */
 const char* cmrt_last_error(const cmrt_ctx* c);
+
+/* ------------------------------------------------------------------------
+ * Batched ensembles.
+ *
+ * The paper steps one lattice at a time; these calls are a library
+ * facility for running many independent lattices of uneven sizes, each the
+ * scheme above with its own parameters (sigma, Lambda, alpha, relaxation
+ * rates, forces, walls), in ONE persistent kernel launch per time step.  The
+ * launch drains a work list of tiles (member, 120-column strip, segment of
+ * rows), longest segments first; no CTA ever waits on another, so there is
+ * no device-side wait that could time out.  Steps are replayed from CUDA
+ * graphs recorded on first use.  Each member's results are bit-identical to
+ * stepping it alone with cmrt_step.
+ * ------------------------------------------------------------------------ */
+
+/* cmrt_batch_tune flag: measure even when the cache holds an entry. */
+#define CMRT_TUNE_FORCE 1
+
+/* Creates an ensemble of n >= 1 lattices on the current device and stream.
+ * params:  cmrt_params[n]; every entry is validated as for cmrt_init, and
+ *          all must share one `precision`.
+ * rho_n0:  array of n pointers (host array), each as rho_n0 of cmrt_init
+ *          for that member (host or device float[ny][nx], or NULL); the
+ *          array itself may be NULL (all members -1).
+ * u0:      likewise, float[2][ny][nx] per member, or NULL.
+ * The batch holds both state buffers of every member in two arenas
+ * (member offsets aligned to 256 B).  Rows per work item start at
+ * min(64, ny) for each size class.  The batch checks the members'
+ * non-finite flags every d steps, d the smallest positive diag_every of the
+ * members (0 everywhere: only at cmrt_batch_diagnostics).
+ * Errors: CMRT_EINVAL (with the member index in the message), CMRT_ENOMEM,
+ * CMRT_ECUDA. */
+cmrt_status cmrt_batch_init(int32_t n, const cmrt_params* params, const float* const* rho_n0,
+                            const float* const* u0, void* cuda_stream, cmrt_batch** out);
+
+/* Advances every member by n >= 0 steps.  Whole blocks of graph_steps steps
+ * are launched as one recorded CUDA graph, the rest one launch per step.
+ * Asynchronous except at the non-finite checks; CMRT_ENONFINITE names the
+ * first member that failed and fails the batch. */
+cmrt_status cmrt_batch_step(cmrt_batch* b, int64_t n);
+
+/* Autotuner: picks the rows per work item of each size class (nx, ny,
+ * wall_y) by coordinate descent over {8, 16, ..., 512} (capped at ny),
+ * two passes, timing whole batched launches (2 warm-up + 5 timed, CUDA
+ * events) that read the current state and write the other buffer, so the
+ * state does not advance.  cache_path (may be NULL): a JSON array, one
+ * object per line, keyed by device name, SM count and the batch signature
+ * (precision, vector path, size classes with their counts); a matching
+ * entry is applied without measuring unless flags has CMRT_TUNE_FORCE, and
+ * a measurement replaces it.  us_per_step (may be NULL) receives the best
+ * time of one batched step in microseconds (the cached one on a hit). */
+cmrt_status cmrt_batch_tune(cmrt_batch* b, const char* cache_path, int32_t flags, double* us_per_step);
+
+/* Sets the rows per work item of the members of size nx x ny with the given
+ * wall_y (CMRT_EINVAL if there are none, or rows < 1).  Rebuilds the work
+ * list after the work queued so far has finished. */
+cmrt_status cmrt_batch_set_rows(cmrt_batch* b, int32_t nx, int32_t ny, int32_t wall_y, int32_t rows);
+
+/* Rows per work item of a size class, -1 if the batch has no such class. */
+int32_t cmrt_batch_get_rows(const cmrt_batch* b, int32_t nx, int32_t ny, int32_t wall_y);
+
+/* Steps per recorded graph: 0 (no graphs) or a positive even number
+ * (default 32). */
+cmrt_status cmrt_batch_set_graph_steps(cmrt_batch* b, int32_t steps);
+
+/* A view of member k as a context: cmrt_fields, cmrt_diagnostics,
+ * cmrt_get_populations, cmrt_set_populations, cmrt_synchronize, cmrt_time
+ * work on it and act on that member's state inside the batch.  cmrt_step on
+ * a view returns CMRT_EINVAL (members advance with cmrt_batch_step), and
+ * cmrt_destroy on a view does nothing: the view belongs to the batch and is
+ * freed by cmrt_batch_destroy.  The same view is returned on every call. */
+cmrt_status cmrt_batch_member(cmrt_batch* b, int32_t k, cmrt_ctx** view);
+
+/* cmrt_diagnostics of every member into out[n][6].  Synchronises. */
+cmrt_status cmrt_batch_diagnostics(cmrt_batch* b, double* out);
+
+/* Waits for all work queued on the batch's stream. */
+cmrt_status cmrt_batch_synchronize(cmrt_batch* b);
+
+/* Number of members, steps taken, kernels launched (every batched step is
+ * one launch, also inside a graph), and work items per step; -1 for NULL. */
+int32_t cmrt_batch_size(const cmrt_batch* b);
+int64_t cmrt_batch_time(const cmrt_batch* b);
+int64_t cmrt_batch_launch_count(const cmrt_batch* b);
+int64_t cmrt_batch_work_items(const cmrt_batch* b);
+
+/* Bytes of device memory the batch holds (arenas, work list, views). */
+size_t cmrt_batch_device_bytes(const cmrt_batch* b);
+
+/* Frees the batch, its member views and everything it allocated.  NULL is a
+ * no-op. */
+void cmrt_batch_destroy(cmrt_batch* b);
+
+/* Message of the last failure on b, or of the last failure in this thread
+ * when b is NULL. */
+const char* cmrt_batch_last_error(const cmrt_batch* b);
 
 #ifdef __cplusplus
 }

@@ -56,9 +56,35 @@ _SIGNATURES = [
     ("cmrt_device_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
     ("cmrt_diagnostics_noalloc", ctypes.c_int, [ctypes.POINTER(cmrt_params), ctypes.c_void_p,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("cmrt_step_vjp", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double)]),
+    ("cmrt_adjoint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_void_p]),
     ("cmrt_destroy", None, [ctypes.c_void_p]),
     ("cmrt_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("cmrt_batch_init", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(cmrt_params), ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("cmrt_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("cmrt_batch_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    ("cmrt_batch_set_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32]),
+    ("cmrt_batch_get_rows", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("cmrt_batch_set_graph_steps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("cmrt_batch_member", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    ("cmrt_batch_diagnostics", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("cmrt_batch_synchronize", ctypes.c_int, [ctypes.c_void_p]),
+    ("cmrt_batch_size", ctypes.c_int32, [ctypes.c_void_p]),
+    ("cmrt_batch_time", ctypes.c_int64, [ctypes.c_void_p]),
+    ("cmrt_batch_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("cmrt_batch_work_items", ctypes.c_int64, [ctypes.c_void_p]),
+    ("cmrt_batch_device_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("cmrt_batch_destroy", None, [ctypes.c_void_p]),
+    ("cmrt_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
+
+CMRT_TUNE_FORCE = 1
 
 _lib = None
 
@@ -89,6 +115,12 @@ class CmrtError(RuntimeError):
 def _check(status, ctx=None):
     if status != CMRT_OK:
         msg = load().cmrt_last_error(ctx)
+        raise CmrtError(status, msg.decode() if msg else "")
+
+
+def _bcheck(status, batch=None):
+    if status != CMRT_OK:
+        msg = load().cmrt_batch_last_error(batch)
         raise CmrtError(status, msg.decode() if msg else "")
 
 
@@ -176,12 +208,113 @@ def cmrt_diagnostics_noalloc(params: cmrt_params, pops_ptr: int, stream_ptr: int
     return vals
 
 
+ADJOINT_PARAMS = ("sigma", "beta", "lambda3_r", "lambda3_b", "g_acc_x", "g_acc_y")
+
+
+def cmrt_step_vjp(ctx, lam_next_ptr: int, lam_ptr: int, grad_params=None):
+    """One-step VJP; adds this step's parameter gradient to ``grad_params`` (list of 6) if given."""
+    g = (ctypes.c_double * 6)(*(grad_params or [0.0] * 6))
+    _check(load().cmrt_step_vjp(ctx, lam_next_ptr, lam_ptr, g), ctx)
+    return list(g)
+
+
+def cmrt_adjoint(ctx, nsteps: int, ckpt_every: int, target_ptr: int, grad_rho_n0_ptr: int = 0):
+    """(J, [dJ/dtheta x 6]) of the colour-field mismatch; dJ/drho^N_0 into grad_rho_n0_ptr if given."""
+    J = ctypes.c_double(0.0)
+    g = (ctypes.c_double * 6)()
+    _check(load().cmrt_adjoint(ctx, int(nsteps), int(ckpt_every), target_ptr, ctypes.byref(J), g,
+                               grad_rho_n0_ptr or None), ctx)
+    return J.value, list(g)
+
+
 def cmrt_destroy(ctx):
     load().cmrt_destroy(ctx)
 
 
 def cmrt_last_error(ctx=None):
     msg = load().cmrt_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def cmrt_batch_init(params_list, rho_n0_ptrs, u0_ptrs, stream_ptr: int):
+    """params_list: sequence of cmrt_params; *_ptrs: sequences of raw pointers (0 = NULL)."""
+    n = len(params_list)
+    arr = (cmrt_params * n)(*params_list)
+    rn = (ctypes.c_void_p * n)(*[p or None for p in rho_n0_ptrs]) if rho_n0_ptrs is not None else None
+    uu = (ctypes.c_void_p * n)(*[p or None for p in u0_ptrs]) if u0_ptrs is not None else None
+    h = ctypes.c_void_p()
+    _bcheck(load().cmrt_batch_init(n, arr, rn, uu, stream_ptr or None, ctypes.byref(h)))
+    return h
+
+
+def cmrt_batch_step(b, n: int):
+    _bcheck(load().cmrt_batch_step(b, int(n)), b)
+
+
+def cmrt_batch_tune(b, cache_path=None, flags: int = 0):
+    us = ctypes.c_double(0.0)
+    path = cache_path.encode() if cache_path else None
+    _bcheck(load().cmrt_batch_tune(b, path, int(flags), ctypes.byref(us)), b)
+    return us.value
+
+
+def cmrt_batch_set_rows(b, nx, ny, wall_y, rows):
+    _bcheck(load().cmrt_batch_set_rows(b, int(nx), int(ny), int(wall_y), int(rows)), b)
+
+
+def cmrt_batch_get_rows(b, nx, ny, wall_y):
+    return load().cmrt_batch_get_rows(b, int(nx), int(ny), int(wall_y))
+
+
+def cmrt_batch_set_graph_steps(b, steps):
+    _bcheck(load().cmrt_batch_set_graph_steps(b, int(steps)), b)
+
+
+def cmrt_batch_member(b, k: int):
+    h = ctypes.c_void_p()
+    _bcheck(load().cmrt_batch_member(b, int(k), ctypes.byref(h)), b)
+    return h
+
+
+def cmrt_batch_diagnostics(b):
+    n = load().cmrt_batch_size(b)
+    out = (ctypes.c_double * (6 * n))()
+    st = load().cmrt_batch_diagnostics(b, out)
+    vals = np.array(list(out)).reshape(n, 6)
+    _bcheck(st, b)
+    return vals
+
+
+def cmrt_batch_synchronize(b):
+    _bcheck(load().cmrt_batch_synchronize(b), b)
+
+
+def cmrt_batch_size(b):
+    return load().cmrt_batch_size(b)
+
+
+def cmrt_batch_time(b):
+    return load().cmrt_batch_time(b)
+
+
+def cmrt_batch_launch_count(b):
+    return load().cmrt_batch_launch_count(b)
+
+
+def cmrt_batch_work_items(b):
+    return load().cmrt_batch_work_items(b)
+
+
+def cmrt_batch_device_bytes(b):
+    return load().cmrt_batch_device_bytes(b)
+
+
+def cmrt_batch_destroy(b):
+    load().cmrt_batch_destroy(b)
+
+
+def cmrt_batch_last_error(b=None):
+    msg = load().cmrt_batch_last_error(b)
     return msg.decode() if msg else ""
 
 
@@ -229,7 +362,26 @@ class Lattice:
         self.ctx = cmrt_init(self._p, _ptr(rn), _ptr(uu), self.stream.cuda_stream)
         self._keep = keep  # device inputs must outlive the queued init kernel
 
+    @classmethod
+    def _view(cls, ctx, params: dict, stream, owner):
+        """A member of a :class:`Batch`: the batch owns the context."""
+        self = cls.__new__(cls)
+        import torch
+        self.torch = torch
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self._p = make_params(params)
+        self.stream = stream
+        self.ctx = ctx
+        self._keep = []
+        self._owner = owner  # keeps the batch (and so this context) alive
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self.ctx = None  # a member view: freed with its batch
+            self._owner = None
+            return
         if getattr(self, "ctx", None):
             cmrt_destroy(self.ctx)
             self.ctx = None
@@ -280,6 +432,26 @@ class Lattice:
     def synchronize(self):
         cmrt_synchronize(self.ctx)
 
+    def step_vjp(self, lam_next):
+        """dJ/df(t) from dJ/df(t+1) for one step at the current state; returns
+        (lam as a (2, 9, ny, nx) CUDA tensor, [dJ/dtheta of this step])."""
+        t = self.torch
+        a = lam_next.to(device="cuda", dtype=t.float32).contiguous() if hasattr(lam_next, "data_ptr") else \
+            t.from_numpy(np.ascontiguousarray(lam_next, dtype=np.float32)).cuda()
+        out = t.empty((2, 9, self.ny, self.nx), dtype=t.float32, device="cuda")
+        g = cmrt_step_vjp(self.ctx, a.data_ptr(), out.data_ptr())
+        return out, g
+
+    def adjoint(self, nsteps: int, target, ckpt_every: int = 200, want_rho_n0: bool = False):
+        """Advance nsteps and return (J, {theta: dJ/dtheta}, dJ/drho^N_0 or None) of
+        J = 1/2 sum (rho^N - target)^2 at the end."""
+        t = self.torch
+        tg = target.to(device="cuda", dtype=t.float32).contiguous() if hasattr(target, "data_ptr") else \
+            t.from_numpy(np.ascontiguousarray(target, dtype=np.float32)).cuda()
+        grn = t.empty((self.ny, self.nx), dtype=t.float32, device="cuda") if want_rho_n0 else None
+        J, g = cmrt_adjoint(self.ctx, nsteps, ckpt_every, tg.data_ptr(), grn.data_ptr() if grn is not None else 0)
+        return J, dict(zip(ADJOINT_PARAMS, g)), grn
+
     @property
     def time(self):
         return cmrt_time(self.ctx)
@@ -287,3 +459,143 @@ class Lattice:
     @property
     def launches(self):
         return cmrt_launch_count(self.ctx)
+
+
+class Batch:
+    """An ensemble of independent lattices stepped by one persistent launch
+    per time step (include/cmrt.h, cmrt_batch_*).
+
+    ``members`` is a sequence of (params dict, rho_n0, u0) triples, the arrays
+    as for :class:`Lattice` (rho_n0 and u0 may be None)."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = [dict(m[0]) for m in members]
+        keep = []
+
+        def as_f32(a):
+            if a is None:
+                return 0
+            if hasattr(a, "data_ptr"):
+                a = a.to(torch.float32).contiguous()
+            else:
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            keep.append(a)
+            return _ptr(a)
+
+        rn = [as_f32(m[1]) for m in members]
+        uu = [as_f32(m[2]) for m in members]
+        self.b = cmrt_batch_init([make_params(p) for p in self.params], rn, uu, self.stream.cuda_stream)
+        self._keep = keep
+        self._views = {}
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self._views.values():
+                v.ctx = None
+                v._owner = None
+            self._views = {}
+            cmrt_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return cmrt_batch_size(self.b)
+
+    def step(self, n: int = 1):
+        cmrt_batch_step(self.b, n)
+
+    def tune(self, cache_path=None, force=False):
+        """Autotune rows per size class; returns the best time of one batched step in us."""
+        return cmrt_batch_tune(self.b, cache_path, CMRT_TUNE_FORCE if force else 0)
+
+    def set_rows(self, nx, ny, wall_y, rows):
+        cmrt_batch_set_rows(self.b, nx, ny, wall_y, rows)
+
+    def get_rows(self, nx, ny, wall_y=0):
+        return cmrt_batch_get_rows(self.b, nx, ny, wall_y)
+
+    def set_graph_steps(self, steps):
+        cmrt_batch_set_graph_steps(self.b, steps)
+
+    def member(self, k: int) -> Lattice:
+        """Lattice view of member k (fields, diagnostics, populations; no step)."""
+        if k not in self._views:
+            ctx = cmrt_batch_member(self.b, k)
+            self._views[k] = Lattice._view(ctx, self.params[k], self.stream, self)
+        return self._views[k]
+
+    def diagnostics(self):
+        """(n, 6) array: mass_r, mass_b, mom_x, mom_y, max|u|, non-finite count per member."""
+        return cmrt_batch_diagnostics(self.b)
+
+    def synchronize(self):
+        cmrt_batch_synchronize(self.b)
+
+    @property
+    def time(self):
+        return cmrt_batch_time(self.b)
+
+    @property
+    def launches(self):
+        return cmrt_batch_launch_count(self.b)
+
+    @property
+    def work_items(self):
+        return cmrt_batch_work_items(self.b)
+
+    @property
+    def device_bytes(self):
+        return cmrt_batch_device_bytes(self.b)
+
+
+def colour_mismatch(theta, rho_n0, params: dict, target, nsteps: int, ckpt_every: int = 200, u0=None):
+    """J = 1/2 sum_r (rho^N(r, nsteps) - target(r))^2 as a differentiable torch
+    function of theta = (sigma, beta, lambda3_r, lambda3_b, g_acc_x, g_acc_y)
+    (float64 tensor) and of the initial colour field rho_n0 (float32 CUDA
+    tensor).  The forward and the adjoint both run in libcmrt."""
+    return _ColourMismatch.apply(theta, rho_n0, params, target, nsteps, ckpt_every, u0)
+
+
+def _autograd_function():
+    import torch
+
+    class ColourMismatch(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, rho_n0, params, target, nsteps, ckpt_every, u0):
+            th = [float(v) for v in theta.detach().cpu().tolist()]
+            d = dict(params)
+            d.update(sigma=th[0], beta=th[1], lambda3_r=th[2], lambda3_b=th[3], g_acc=(th[4], th[5]))
+            lat = Lattice(d, rho_n0.detach(), u0)
+            J, g, grn = lat.adjoint(nsteps, target, ckpt_every=ckpt_every, want_rho_n0=True)
+            lat.close()
+            ctx.save_for_backward(torch.tensor([g[k] for k in ADJOINT_PARAMS], dtype=torch.float64), grn)
+            ctx.theta_device = theta.device
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g, grn = ctx.saved_tensors
+            gJ = gJ.detach().to(torch.float64).cpu()
+            return (gJ * g).to(ctx.theta_device), (grn * float(gJ)), None, None, None, None, None
+
+    return ColourMismatch
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *args):
+        if _Lazy.fn is None:
+            _Lazy.fn = _autograd_function()
+        return _Lazy.fn.apply(*args)
+
+
+_ColourMismatch = _Lazy()

@@ -1,0 +1,704 @@
+// Discrete adjoint (reverse mode) of the fused chromodynamic MRT step
+// (arXiv 2005.04642, Sec. 2, App. A) for FP32 storage.
+//
+// The forward step maps the post-collision state P_{t-1} to P_t:
+//   f(t) = gather(P_{t-1})                       (streaming, Eq. equ_evolution)
+//   P_t  = CR(f(t))                              (collide + recolour)
+// with CR built from the moments, grad rho^N, the unit normal, the curvature,
+// the force and force-adjusted velocity, grad Phi', div u, the correction
+// tensor, the MRT collision and the recolour.  Its adjoint is
+//   lam_P(t-1) = gather^T( CR'(f(t))^T lam_P(t) ),
+// evaluated here as a chain of per-node passes over whole planes (one thread
+// per node), the reverse of the forward chain:
+//   k_fwd_moments   rho_R, rho_B, j, colour fractions, Phi'  (recomputed)
+//   k_fwd_normal    grad rho^N                             (recomputed)
+//   k_fwd_force     K, G, u                                (recomputed)
+//   k_rev_collide   reverse of recolour, reconstruction, relaxation,
+//                   equilibria, sources, correction tensor, lambda_3
+//   k_rev_force     reverse of div u and of u = (j + G/2)/rho, G
+//   k_rev_normal    reverse of K = div n-hat and n-hat = -g/max(|g|, eps)
+//   k_rev_moments   reverse of grad rho^N, grad Phi', rho^N, Phi'
+//   k_rev_gather    transpose of the streaming gather (bounce-back included)
+// The transposed compact stencils are gathers: on a periodic lattice the
+// transpose of d/dx is -d/dx; next to a wall the mirrored ghost reads add
+// the terms of the row's own nodes with the ghost's parity.
+//
+// Parameter gradients (sigma, beta, lambda3_r, lambda3_b, g_acc) are reduced
+// per CTA in FP64 and accumulated across steps in a per-CTA FP64 slot (no
+// atomics: every launch of a pass uses the same grid, and the slots are
+// summed once at the end).
+#include "cmrt_device.cuh"
+
+namespace cmrt {
+namespace {
+
+constexpr int kAT = 128;  // threads per CTA (along x)
+
+// Scratch planes, each float[ny][nx].
+enum Plane : int {
+    kRR = 0, kRB, kJX, kJY, kCHR, kCHB, kPHIP, kGX, kGY, kK, kGFX, kGFY, kUX, kUY,  // forward
+    kFB0,                                                                   // 9 planes f-bar
+    kRRB = kFB0 + 9, kRBB, kUXB, kUYB, kGFXB, kGFYB, kDPXB, kDPYB, kDIVUB, kGXB, kGYB, kRNB, kJXB, kJYB, kKB,
+    kNumPlanes
+};
+static_assert(kNumPlanes == kAdjPlanes, "scratch plane count");
+
+struct Lat {
+    int nx, ny, walls;
+    size_t n;
+    __device__ __forceinline__ size_t at(int x, int y) const { return static_cast<size_t>(y) * nx + x; }
+    __device__ __forceinline__ int wx(int x) const {
+        int r = x % nx;
+        return r < 0 ? r + nx : r;
+    }
+    __device__ __forceinline__ int wy(int y) const {
+        int r = y % ny;
+        return r < 0 ? r + ny : r;
+    }
+    // value of a plane at (x, y) (x periodic; y periodic, or mirrored across
+    // the wall planes with the given parity)
+    __device__ __forceinline__ float val(const float* a, int x, int y, float parity) const {
+        x = wx(x);
+        if (!walls) return a[at(x, wy(y))];
+        if (y < 0) return parity * a[at(x, -1 - y)];
+        if (y >= ny) return parity * a[at(x, 2 * ny - 1 - y)];
+        return a[at(x, y)];
+    }
+    // compact gradient (Sec. 2) of a plane at (x, y)
+    __device__ __forceinline__ void grad(const float* a, int x, int y, float parity, float& gx, float& gy) const {
+        const float e = val(a, x + 1, y, parity), w = val(a, x - 1, y, parity);
+        const float n_ = val(a, x, y + 1, parity), s = val(a, x, y - 1, parity);
+        const float ne = val(a, x + 1, y + 1, parity), nw = val(a, x - 1, y + 1, parity);
+        const float se = val(a, x + 1, y - 1, parity), sw = val(a, x - 1, y - 1, parity);
+        gx = ddx(e, w, ne, nw, se, sw);
+        gy = ddy(n_, s, ne, nw, se, sw);
+    }
+    // transpose of one component (XC: x, else y) of the compact gradient,
+    // applied to a plane: sum_i 3 w_i c_i a(r - c_i) over nodes r - c_i of
+    // the lattice, plus, in a wall row, the row's own nodes whose stencil
+    // read this node as a mirrored ghost
+    template <bool XC>
+    __device__ __forceinline__ float gradT(const float* a, int x, int y, float parity) const {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int c = XC ? lcx(i) : lcy(i);
+            if (c == 0) continue;
+            const float k = 3.0f * lw(i) * float(c);
+            const int sy = y - lcy(i);
+            if (!walls || (sy >= 0 && sy < ny)) acc = fmaf(k, a[at(wx(x - lcx(i)), wy(sy))], acc);
+            if (walls) {
+                if (y == 0 && lcy(i) == -1) acc = fmaf(parity * k, a[at(wx(x - lcx(i)), 0)], acc);
+                if (y == ny - 1 && lcy(i) == 1) acc = fmaf(parity * k, a[at(wx(x - lcx(i)), ny - 1)], acc);
+            }
+        }
+        return acc;
+    }
+};
+
+__device__ __forceinline__ Lat lattice(const StepParams& P) {
+    return Lat{P.nx, P.ny, P.wall_y, static_cast<size_t>(P.nx) * P.ny};
+}
+
+// pre-collision populations of node (x, y): f_i(r) = P_i(r - c_i), or
+// P_opp(i)(r) where r - c_i lies beyond a wall (half-way bounce-back)
+__device__ __forceinline__ void gather_node(const float* __restrict__ post, const Lat& L, int x, int y,
+                                            float (&fr)[9], float (&fb)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int sy = y - lcy(i);
+        size_t o;
+        int li = i;
+        if (L.walls && (sy < 0 || sy >= L.ny)) {
+            li = lopp(i);
+            o = L.at(x, y);
+        } else {
+            o = L.at(L.wx(x - lcx(i)), L.wy(sy));
+        }
+        fr[i] = post[static_cast<size_t>(li) * L.n + o];
+        fb[i] = post[static_cast<size_t>(9 + li) * L.n + o];
+    }
+}
+
+__device__ __forceinline__ float sum9f(const float (&v)[9]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// adjoint of g -> g / max(|g|, eps): (I - e e^T) b / |g| above eps, b / eps below
+__device__ __forceinline__ void normalise_T(float gx, float gy, float bx, float by, float& ox, float& oy) {
+    const float mag2 = fmaf(gx, gx, gy * gy);
+    if (mag2 >= kNormalEps * kNormalEps) {
+        const float inv = rsqrtf(mag2);
+        const float ex = gx * inv, ey = gy * inv;
+        const float dot = fmaf(ex, bx, ey * by);
+        ox = (bx - ex * dot) * inv;
+        oy = (by - ey * dot) * inv;
+    } else {
+        ox = bx * (1.0f / kNormalEps);
+        oy = by * (1.0f / kNormalEps);
+    }
+}
+
+// FP64 CTA reduction of up to 7 values, added into this CTA's slot.
+template <int N>
+__device__ __forceinline__ void add_partials(double (&v)[N], const int* slots, double* __restrict__ partials) {
+    __shared__ double red[kAT / 32][N];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) red[warp][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double acc = 0.0;
+        for (int w = 0; w < kAT / 32; ++w) acc += red[w][threadIdx.x];
+        const size_t b = static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[b * kAdjSlots + slots[threadIdx.x]] += acc;
+    }
+}
+
+// ----------------------------------------------------------------- forward recomputation
+__global__ void __launch_bounds__(kAT) k_fwd_moments(const float* __restrict__ post, const StepParams P,
+                                                      float* __restrict__ S) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    float fr[9], fb[9];
+    gather_node(post, L, x, y, fr, fb);
+    const float rr = sum9f(fr), rb = sum9f(fb);
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
+    const size_t o = L.at(x, y);
+    S[kRR * L.n + o] = rr;
+    S[kRB * L.n + o] = rb;
+    S[kJX * L.n + o] = ((f[1] + f[7]) + f[8]) - ((f[3] + f[5]) + f[4]);
+    S[kJY * L.n + o] = ((f[1] + f[3]) + f[2]) - ((f[5] + f[7]) + f[6]);
+    // colour fractions chi_R = a / (a + b), chi_B = b / (a + b), rho^N = chi_R - chi_B
+    // (Eq. equ_rhoN_def); the smaller one carries the colour gradient of a
+    // nearly pure region without the cancellation of rho^N near -1 or +1
+    const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
+    const float inv = 1.0f / (a + b);
+    S[kCHR * L.n + o] = a * inv;
+    S[kCHB * L.n + o] = b * inv;
+    S[kPHIP * L.n + o] = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
+}
+
+__global__ void __launch_bounds__(kAT) k_fwd_normal(const StepParams P, float* __restrict__ S) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    // grad rho^N = 2 grad chi_R = -2 grad chi_B (the stencil weights sum to
+    // zero): the same stencil, evaluated on the fraction that is small here
+    const size_t o = L.at(x, y);
+    float gx, gy;
+    if (S[kCHR * L.n + o] < S[kCHB * L.n + o]) {
+        L.grad(S + kCHR * L.n, x, y, 1.0f, gx, gy);
+        gx *= 2.0f;
+        gy *= 2.0f;
+    } else {
+        L.grad(S + kCHB * L.n, x, y, 1.0f, gx, gy);
+        gx *= -2.0f;
+        gy *= -2.0f;
+    }
+    S[kGX * L.n + o] = gx;
+    S[kGY * L.n + o] = gy;
+}
+
+__device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& ny) {
+    const float mag2 = fmaf(gx, gx, gy * gy);
+    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    nx = -gx * inv;
+    ny = -gy * inv;
+}
+
+__global__ void __launch_bounds__(kAT) k_fwd_force(const StepParams P, float* __restrict__ S) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    float K = P.fixed_K;
+    if (P.curvature_mode == 0) {
+        // K = div n-hat with n-hat of the neighbours (x even, y odd beyond a wall)
+        float nxv[9], nyv[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int yy = y + lcy(i);
+            const bool ghost = L.walls && (yy < 0 || yy >= L.ny);
+            const int ys = !L.walls ? L.wy(yy) : (yy < 0 ? -1 - yy : (yy >= L.ny ? 2 * L.ny - 1 - yy : yy));
+            const size_t o = L.at(L.wx(x + lcx(i)), ys);
+            normal_of(S[kGX * L.n + o], S[kGY * L.n + o], nxv[i], nyv[i]);
+            if (ghost) nyv[i] = -nyv[i];
+        }
+        K = ddx(nxv[8], nxv[4], nxv[1], nxv[3], nxv[7], nxv[5]) + ddy(nyv[2], nyv[6], nyv[1], nyv[3], nyv[7], nyv[5]);
+    }
+    const size_t o = L.at(x, y);
+    const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
+    const float rho = S[kRR * L.n + o] + S[kRB * L.n + o];
+    const float hk = P.half_sigma * K;
+    const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
+    const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
+    S[kK * L.n + o] = K;
+    S[kGFX * L.n + o] = Gx;
+    S[kGFY * L.n + o] = Gy;
+    S[kUX * L.n + o] = fmaf(0.5f, Gx, S[kJX * L.n + o]) / rho;
+    S[kUY * L.n + o] = fmaf(0.5f, Gy, S[kJY * L.n + o]) / rho;
+}
+
+// ----------------------------------------------------------------- reverse passes
+// Reverse of the per-node collision and recolour (App. A Eqs. 38, eq84;
+// Eq. eq_re_color).  lam: adjoint of the post-collision state P_t (18 planes).
+__global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ post, const float* __restrict__ lam,
+                                                      const StepParams P, float* __restrict__ S,
+                                                      double* __restrict__ partials) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    double acc[3] = {0.0, 0.0, 0.0};  // beta, lambda3_r, lambda3_b
+    if (x < L.nx) {
+        const size_t o = L.at(x, y);
+        float fr[9], fb[9], f[9];
+        gather_node(post, L, x, y, fr, fb);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
+        const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
+        const float rho = rr + rb, ir = 1.0f / rho, ir2 = ir * ir;
+        const float ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
+        const float Gx = S[kGFX * L.n + o], Gy = S[kGFY * L.n + o];
+        const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
+        const float rn = S[kCHR * L.n + o] - S[kCHB * L.n + o];
+        float dPx, dPy, dux, duy, t0, t1;
+        L.grad(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
+        L.grad(S + kUX * L.n, x, y, -1.0f, dux, t0);
+        L.grad(S + kUY * L.n, x, y, -1.0f, t1, duy);
+        const float divu = dux + duy;
+        // ---- forward values at this node
+        float nu, dnu_drn = 0.0f;
+        if (P.visc_mode == 0) {
+            nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
+            dnu_drn = 0.5f * (P.nu_r - P.nu_b);
+        } else {
+            nu = P.eta * ir;
+        }
+        const float lam3 = 2.0f / fmaf(6.0f, nu, 1.0f);
+        const float a = fmaf(-0.5f, lam3, 1.0f);
+        const float hx = Gx - dPx, hy = Gy - dPy;
+        const float iso = fmaf(ux, dPx, fmaf(uy, dPy, -rho * divu * (1.0f / 3.0f)));
+        const float Cxx = a * fmaf(2.0f * ux, hx, -iso);
+        const float Cyy = a * fmaf(2.0f * uy, hy, -iso);
+        const float Cxy = a * fmaf(ux, hy, uy * hx);
+        float m[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float h = p == 0 ? 1.0f : p == 1 ? float(lcx(i)) : p == 2 ? float(lcy(i))
+                              : p == 3 ? float(lcx(i) * lcx(i)) : p == 4 ? float(lcy(i) * lcy(i))
+                              : p == 5 ? float(lcx(i) * lcy(i)) : p == 6 ? lg(i)
+                              : p == 7 ? lg(i) * float(lcx(i)) : lg(i) * float(lcy(i));
+                if (h != 0.0f) s = fmaf(h, f[i], s);
+            }
+            m[p] = s;
+        }
+        const float pres = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+        float meq[9] = {rho, rho * ux, rho * uy, fmaf(rho * ux, ux, pres), fmaf(rho * uy, uy, pres), rho * ux * uy,
+                        P.ghost_N_mode == 0 ? fmaf(P.neq_r, rr, P.neq_b * rb) : 0.0f, 0.0f, 0.0f};
+        const float lamv[9] = {0.0f, 0.0f, 0.0f, lam3, lam3, lam3, P.lambda6, P.lambda7, P.lambda7};
+        const float Sv[9] = {0.0f, Gx, Gy, Cxx, Cyy, Cxy, 0.0f, 0.0f, 0.0f};
+        float fp[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float s = f[i];
+#pragma unroll
+            for (int p = 0; p < 9; ++p) {
+                const float k = kinv(i, p);
+                if (k != 0.0f) s = fmaf(k, fmaf(lamv[p], meq[p] - m[p], Sv[p]), s);
+            }
+            fp[i] = s;
+        }
+        const float mag2 = fmaf(gx, gx, gy * gy);
+        const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+        const float ex = gx * inv, ey = gy * inv;
+        const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * ir;  // phi_i = w_i phim (i != 0)
+        const float seg = P.beta * rr * rb * ir;
+        // ---- recolour: C++_i = x_C f+_i +/- seg phi_i (e . c-hat_i)
+        const float xR = rr * ir, xB = rb * ir;
+        float fpb[9];
+        float xRb = 0.0f, xBb = 0.0f, segb = 0.0f, phimb = 0.0f, exb = 0.0f, eyb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float lr = lam[static_cast<size_t>(i) * L.n + o];
+            const float lb = lam[static_cast<size_t>(9 + i) * L.n + o];
+            fpb[i] = fmaf(xR, lr, xB * lb);
+            xRb = fmaf(lr, fp[i], xRb);
+            xBb = fmaf(lb, fp[i], xBb);
+            if (i > 0) {
+                const float db = lr - lb;
+                const float ec = fmaf(chx(i), ex, chy(i) * ey);
+                segb = fmaf(db * lw(i) * phim, ec, segb);
+                phimb = fmaf(db * seg * lw(i), ec, phimb);
+                exb = fmaf(db * seg * lw(i) * phim, chx(i), exb);
+                eyb = fmaf(db * seg * lw(i) * phim, chy(i), eyb);
+            }
+        }
+        acc[0] = static_cast<double>(segb) * (rr * rb * ir);
+        float rrb = (xRb - xBb) * rb * ir2;
+        float rbb = (xBb - xRb) * rr * ir2;
+        rrb = fmaf(segb * P.beta, rb * rb * ir2, rrb);
+        rbb = fmaf(segb * P.beta, rr * rr * ir2, rbb);
+        rrb = fmaf(phimb * (P.kphi_r - P.kphi_b), rb * ir2, rrb);
+        rbb = fmaf(phimb * (P.kphi_b - P.kphi_r), rr * ir2, rbb);
+        float gxb, gyb;
+        normalise_T(gx, gy, exb, eyb, gxb, gyb);
+        // ---- reconstruction and relaxation: m+ = m + lambda (m^(0) - m) + S, f+ = M^{-1} m+
+        float mpb[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float k = kinv(i, p);
+                if (k != 0.0f) s = fmaf(k, fpb[i], s);
+            }
+            mpb[p] = s;
+        }
+        float lam3b = 0.0f;
+#pragma unroll
+        for (int p = 3; p < 6; ++p) lam3b = fmaf(mpb[p], meq[p] - m[p], lam3b);
+        float mb[9], meqb[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            mb[p] = (1.0f - lamv[p]) * mpb[p];
+            meqb[p] = lamv[p] * mpb[p];
+        }
+        // common part of the population adjoint, M^T m-bar
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float fbi = mb[0] + float(lcx(i)) * mb[1] + float(lcy(i)) * mb[2] +
+                              float(lcx(i) * lcx(i)) * mb[3] + float(lcy(i) * lcy(i)) * mb[4] +
+                              float(lcx(i) * lcy(i)) * mb[5] + lg(i) * (mb[6] + float(lcx(i)) * mb[7] +
+                                                                        float(lcy(i)) * mb[8]);
+            S[static_cast<size_t>(kFB0 + i) * L.n + o] = fbi;
+        }
+        // modal equilibrium (App. A)
+        float rhob = meqb[0] + meqb[1] * ux + meqb[2] * uy + meqb[3] * ux * ux + meqb[4] * uy * uy +
+                     meqb[5] * ux * uy;
+        float uxb = rho * (meqb[1] + 2.0f * ux * meqb[3] + uy * meqb[5]);
+        float uyb = rho * (meqb[2] + 2.0f * uy * meqb[4] + ux * meqb[5]);
+        const float prb = meqb[3] + meqb[4];
+        rrb = fmaf(P.cs2_r, prb, rrb);
+        rbb = fmaf(P.cs2_b, prb, rbb);
+        if (P.ghost_N_mode == 0) {
+            rrb = fmaf(P.neq_r, meqb[6], rrb);
+            rbb = fmaf(P.neq_b, meqb[6], rbb);
+        }
+        // sources S = (0, G, C_xx, C_yy, C_xy, 0, 0, 0) and the correction tensor (Eq. Correction)
+        float Gxb = mpb[1], Gyb = mpb[2];
+        const float cxxb = mpb[3], cyyb = mpb[4], cxyb = mpb[5];
+        const float ab = cxxb * fmaf(2.0f * ux, hx, -iso) + cyyb * fmaf(2.0f * uy, hy, -iso) +
+                         cxyb * fmaf(ux, hy, uy * hx);
+        lam3b = fmaf(-0.5f, ab, lam3b);
+        const float isob = -a * (cxxb + cyyb);
+        const float hxb = a * fmaf(2.0f * ux, cxxb, uy * cxyb);
+        const float hyb = a * fmaf(2.0f * uy, cyyb, ux * cxyb);
+        uxb += a * fmaf(2.0f * hx, cxxb, hy * cxyb) + isob * dPx;
+        uyb += a * fmaf(2.0f * hy, cyyb, hx * cxyb) + isob * dPy;
+        Gxb += hxb;
+        Gyb += hyb;
+        const float dPxb = fmaf(isob, ux, -hxb);
+        const float dPyb = fmaf(isob, uy, -hyb);
+        rhob = fmaf(-isob * (1.0f / 3.0f), divu, rhob);
+        const float divub = -isob * rho * (1.0f / 3.0f);
+        // lambda_3 = 2 / (6 nu + 1): d lambda_3 / d nu = -3 lambda_3^2
+        const float nub = lam3b * (-3.0f * lam3 * lam3);
+        float rnb = 0.0f;
+        if (P.visc_mode == 0) {
+            rnb = nub * dnu_drn;
+            // nu_C = (2 / lambda3_C - 1) / 6: d nu_C / d lambda3_C = -(6 nu_C + 1)^2 / 12
+            const float dr = fmaf(6.0f, P.nu_r, 1.0f), db = fmaf(6.0f, P.nu_b, 1.0f);
+            acc[1] = static_cast<double>(nub * 0.5f * (1.0f + rn)) * (-(double)dr * dr / 12.0);
+            acc[2] = static_cast<double>(nub * 0.5f * (1.0f - rn)) * (-(double)db * db / 12.0);
+        } else {
+            rhob = fmaf(nub, -P.eta * ir2, rhob);
+        }
+        S[kRRB * L.n + o] = rrb + rhob;
+        S[kRBB * L.n + o] = rbb + rhob;
+        S[kUXB * L.n + o] = uxb;
+        S[kUYB * L.n + o] = uyb;
+        S[kGFXB * L.n + o] = Gxb;
+        S[kGFYB * L.n + o] = Gyb;
+        S[kDPXB * L.n + o] = dPxb;
+        S[kDPYB * L.n + o] = dPyb;
+        S[kDIVUB * L.n + o] = divub;
+        S[kGXB * L.n + o] = gxb;
+        S[kGYB * L.n + o] = gyb;
+        S[kRNB * L.n + o] = rnb;
+    }
+    const int slots[3] = {1, 2, 3};
+    add_partials<3>(acc, slots, partials);
+}
+
+// Reverse of div u, u = (j + G/2) / rho and G = sigma K g / 2 + rho g_acc + g_vol.
+__global__ void __launch_bounds__(kAT) k_rev_force(const StepParams P, float* __restrict__ S,
+                                                    double* __restrict__ partials) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    double acc[3] = {0.0, 0.0, 0.0};  // sigma, g_acc_x, g_acc_y
+    if (x < L.nx) {
+        const size_t o = L.at(x, y);
+        const float uxt = S[kUXB * L.n + o] + L.gradT<true>(S + kDIVUB * L.n, x, y, -1.0f);
+        const float uyt = S[kUYB * L.n + o] + L.gradT<false>(S + kDIVUB * L.n, x, y, -1.0f);
+        const float rho = S[kRR * L.n + o] + S[kRB * L.n + o];
+        const float ir = 1.0f / rho;
+        const float ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
+        const float Gxt = fmaf(0.5f * ir, uxt, S[kGFXB * L.n + o]);
+        const float Gyt = fmaf(0.5f * ir, uyt, S[kGFYB * L.n + o]);
+        const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o], K = S[kK * L.n + o];
+        const float rhob = -(ux * uxt + uy * uyt) * ir + Gxt * P.gacc_x + Gyt * P.gacc_y;
+        const float gG = fmaf(Gxt, gx, Gyt * gy);
+        S[kJXB * L.n + o] = uxt * ir;
+        S[kJYB * L.n + o] = uyt * ir;
+        S[kKB * L.n + o] = P.half_sigma * gG;
+        S[kGXB * L.n + o] += P.half_sigma * K * Gxt;
+        S[kGYB * L.n + o] += P.half_sigma * K * Gyt;
+        S[kRRB * L.n + o] += rhob;
+        S[kRBB * L.n + o] += rhob;
+        acc[0] = 0.5 * static_cast<double>(K) * gG;
+        acc[1] = static_cast<double>(rho) * Gxt;
+        acc[2] = static_cast<double>(rho) * Gyt;
+    }
+    const int slots[3] = {0, 4, 5};
+    add_partials<3>(acc, slots, partials);
+}
+
+// Reverse of K = d_x n_x + d_y n_y and n-hat = -g / max(|g|, eps).
+__global__ void __launch_bounds__(kAT) k_rev_normal(const StepParams P, float* __restrict__ S) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+    const float nxb = L.gradT<true>(S + kKB * L.n, x, y, 1.0f);
+    const float nyb = L.gradT<false>(S + kKB * L.n, x, y, -1.0f);
+    float tx, ty;
+    normalise_T(S[kGX * L.n + o], S[kGY * L.n + o], nxb, nyb, tx, ty);
+    S[kGXB * L.n + o] -= tx;
+    S[kGYB * L.n + o] -= ty;
+}
+
+// Reverse of grad rho^N, grad Phi', rho^N, Phi' and of the moments: leaves
+// the population adjoint dJ/dC_i(r, t) = FB_i + (c_i . j-bar) + rho_C-bar.
+__global__ void __launch_bounds__(kAT) k_rev_moments(const StepParams P, float* __restrict__ S) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+    const float rnb = S[kRNB * L.n + o] + L.gradT<true>(S + kGXB * L.n, x, y, 1.0f) +
+                      L.gradT<false>(S + kGYB * L.n, x, y, 1.0f);
+    const float phb = L.gradT<true>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false>(S + kDPYB * L.n, x, y, 1.0f);
+    const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
+    const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
+    const float iden = 1.0f / ((a + b) * (a + b));
+    S[kRRB * L.n + o] += fmaf(rnb * 2.0f * b * iden, P.inv_rho0_r, phb * P.phip_r);
+    S[kRBB * L.n + o] += fmaf(rnb * -2.0f * a * iden, P.inv_rho0_b, phb * P.phip_b);
+    const float jxb = S[kJXB * L.n + o], jyb = S[kJYB * L.n + o];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        float v = S[static_cast<size_t>(kFB0 + i) * L.n + o];
+        if (lcx(i)) v += float(lcx(i)) * jxb;
+        if (lcy(i)) v += float(lcy(i)) * jyb;
+        S[static_cast<size_t>(kFB0 + i) * L.n + o] = v;
+    }
+}
+
+// Transpose of the streaming gather: lam_i(s) = fbar_i(s + c_i), or
+// fbar_opp(i)(s) where s + c_i lies beyond a wall.
+__global__ void __launch_bounds__(kAT) k_rev_gather(const StepParams P, const float* __restrict__ S,
+                                                     float* __restrict__ lam_out) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ty = y + lcy(i);
+        size_t src;
+        int li = i;
+        if (L.walls && (ty < 0 || ty >= L.ny)) {
+            li = lopp(i);
+            src = o;
+        } else {
+            src = L.at(L.wx(x + lcx(i)), L.wy(ty));
+        }
+        const float common = S[static_cast<size_t>(kFB0 + li) * L.n + src];
+        lam_out[static_cast<size_t>(i) * L.n + o] = common + S[kRRB * L.n + src];
+        lam_out[static_cast<size_t>(9 + i) * L.n + o] = common + S[kRBB * L.n + src];
+    }
+}
+
+// dJ/df(t) in the public pre-collision layout: fbar_i + rho_C-bar at the node.
+__global__ void __launch_bounds__(kAT) k_rev_expand(const StepParams P, const float* __restrict__ S,
+                                                     float* __restrict__ lam_pre) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float common = S[static_cast<size_t>(kFB0 + i) * L.n + o];
+        lam_pre[static_cast<size_t>(i) * L.n + o] = common + S[kRRB * L.n + o];
+        lam_pre[static_cast<size_t>(9 + i) * L.n + o] = common + S[kRBB * L.n + o];
+    }
+}
+
+// Objective J = 1/2 sum (rho^N - target)^2 of f(T) = gather(P_{T-1}) and its
+// gradient dJ/dC_i = (rho^N - target) d rho^N / d rho_C, the same for every link.
+__global__ void __launch_bounds__(kAT) k_seed(const float* __restrict__ post, const float* __restrict__ target,
+                                               const StepParams P, float* __restrict__ S,
+                                               double* __restrict__ partials) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    double acc[1] = {0.0};
+    if (x < L.nx) {
+        const size_t o = L.at(x, y);
+        float fr[9], fb[9];
+        gather_node(post, L, x, y, fr, fb);
+        const float a = sum9f(fr) * P.inv_rho0_r, b = sum9f(fb) * P.inv_rho0_b;
+        const float res = (a - b) / (a + b) - target[o];
+        const float iden = 1.0f / ((a + b) * (a + b));
+        acc[0] = 0.5 * static_cast<double>(res) * res;
+        S[kRRB * L.n + o] = res * 2.0f * b * iden * P.inv_rho0_r;
+        S[kRBB * L.n + o] = res * -2.0f * a * iden * P.inv_rho0_b;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) S[static_cast<size_t>(kFB0 + i) * L.n + o] = 0.0f;
+    }
+    const int slots[1] = {6};
+    add_partials<1>(acc, slots, partials);
+}
+
+// dJ/drho^N_0 through the initial state C_i = (rho_C / rho) f^(0)_i(rho, u_0),
+// rho_R = rho0_r (1 + rho^N_0)/2, rho_B = rho0_b (1 - rho^N_0)/2; pre0 is that
+// state (pre-collision, public layout), lam0 its adjoint.
+__global__ void __launch_bounds__(kAT) k_init_T(const float* __restrict__ pre0, const float* __restrict__ lam0,
+                                                 const StepParams P, float* __restrict__ grad) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+    float R[9], B[9], f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        R[i] = pre0[static_cast<size_t>(i) * L.n + o];
+        B[i] = pre0[static_cast<size_t>(9 + i) * L.n + o];
+        f[i] = R[i] + B[i];
+    }
+    const float rr = sum9f(R), rb = sum9f(B), rho = rr + rb, ir = 1.0f / rho, ir2 = ir * ir;
+    const float ux = (((f[1] + f[7]) + f[8]) - ((f[3] + f[5]) + f[4])) * ir;
+    const float uy = (((f[1] + f[3]) + f[2]) - ((f[5] + f[7]) + f[6])) * ir;
+    const float xR = rr * ir, xB = rb * ir;
+    float xRb = 0.0f, xBb = 0.0f, rrb = 0.0f, rbb = 0.0f;
+    const float usq = fmaf(ux, ux, uy * uy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float lr = lam0[static_cast<size_t>(i) * L.n + o];
+        const float lb = lam0[static_cast<size_t>(9 + i) * L.n + o];
+        xRb = fmaf(lr, f[i], xRb);
+        xBb = fmaf(lb, f[i], xBb);
+        const float f0b = fmaf(xR, lr, xB * lb);
+        const float cu = fmaf(float(lcx(i)), ux, float(lcy(i)) * uy);
+        const float Q = fmaf(3.0f, cu, fmaf(4.5f * cu, cu, -1.5f * usq));
+        // rho phi_0 = alpha_r rho_R + alpha_b rho_B; rho phi_i = k w_i ((1 - alpha_r) rho_R + (1 - alpha_b) rho_B)
+        const float kr = i == 0 ? P.alpha_r : lw(i) * P.kphi_r;
+        const float kb = i == 0 ? P.alpha_b : lw(i) * P.kphi_b;
+        rrb = fmaf(f0b, fmaf(lw(i), Q, kr), rrb);
+        rbb = fmaf(f0b, fmaf(lw(i), Q, kb), rbb);
+    }
+    rrb = fmaf(xRb - xBb, rb * ir2, rrb);
+    rbb = fmaf(xBb - xRb, rr * ir2, rbb);
+    // d rho_R / d rho^N_0 = rho0_r / 2, d rho_B / d rho^N_0 = -rho0_b / 2
+    grad[o] = 0.5f * (rrb / P.inv_rho0_r - rbb / P.inv_rho0_b);
+}
+
+__global__ void k_adj_reduce(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    __shared__ double red[kAT / 32][kAdjSlots];
+    double v[kAdjSlots];
+#pragma unroll
+    for (int j = 0; j < kAdjSlots; ++j) v[j] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < kAdjSlots; ++j) v[j] += partials[static_cast<size_t>(b) * kAdjSlots + j];
+#pragma unroll
+    for (int j = 0; j < kAdjSlots; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < kAdjSlots; ++j) red[warp][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x < kAdjSlots) {
+        double acc = 0.0;
+        for (int w = 0; w < kAT / 32; ++w) acc += red[w][threadIdx.x];
+        out[threadIdx.x] = acc;
+    }
+}
+
+dim3 adj_grid(const StepParams& P) { return dim3(static_cast<unsigned>((P.nx + kAT - 1) / kAT), P.ny, 1); }
+
+// the reverse passes shared by both forms of one adjoint step
+cudaError_t reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
+                         cudaStream_t s) {
+    const dim3 g = adj_grid(P);
+    k_fwd_moments<<<g, kAT, 0, s>>>(post, P, S);
+    k_fwd_normal<<<g, kAT, 0, s>>>(P, S);
+    k_fwd_force<<<g, kAT, 0, s>>>(P, S);
+    k_rev_collide<<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
+    k_rev_force<<<g, kAT, 0, s>>>(P, S, partials);
+    if (P.curvature_mode == 0) k_rev_normal<<<g, kAT, 0, s>>>(P, S);
+    k_rev_moments<<<g, kAT, 0, s>>>(P, S);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int adj_blocks(int nx, int ny) { return ((nx + kAT - 1) / kAT) * ny; }
+
+int adj_launches_per_step(const StepParams& P) { return P.curvature_mode == 0 ? 8 : 7; }
+
+cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
+                                double* partials, float* lam_prev, cudaStream_t s) {
+    cudaError_t e = reverse_core(post, lam_post, P, scratch, partials, s);
+    if (e != cudaSuccess) return e;
+    k_rev_gather<<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_prev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
+                                    double* partials, float* lam_pre, cudaStream_t s) {
+    cudaError_t e = reverse_core(post, lam_post, P, scratch, partials, s);
+    if (e != cudaSuccess) return e;
+    k_rev_expand<<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_seed(const float* post, const float* target, const StepParams& P, float* scratch,
+                                double* partials, float* lam_post, cudaStream_t s) {
+    const dim3 g = adj_grid(P);
+    k_seed<<<g, kAT, 0, s>>>(post, target, P, scratch, partials);
+    k_rev_gather<<<g, kAT, 0, s>>>(P, scratch, lam_post);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(const float* pre0, const float* lam_pre0, const StepParams& P, float* grad_rho_n0,
+                                cudaStream_t s) {
+    k_init_T<<<adj_grid(P), kAT, 0, s>>>(pre0, lam_pre0, P, grad_rho_n0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_reduce(const double* partials, int nblocks, double* out, cudaStream_t s) {
+    k_adj_reduce<<<1, kAT, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cmrt

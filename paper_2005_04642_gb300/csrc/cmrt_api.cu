@@ -4,8 +4,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "cmrt.h"
 #include "cmrt_internal.h"
@@ -15,6 +18,14 @@ using cmrt::StepParams;
 namespace {
 
 thread_local std::string g_thread_error;
+
+struct Batch;
+
+// Device staging for host-pointer arguments (grown on demand).
+struct Staging {
+    float* ptr = nullptr;
+    size_t bytes = 0;
+};
 
 struct Ctx {
     cmrt_params p{};
@@ -27,8 +38,20 @@ struct Ctx {
     double* d_partials = nullptr;        // per-CTA partial diagnostics
     double* d_diag = nullptr;            // reduced diagnostics
     int n_partials = 0;
-    float* staging = nullptr;            // device staging for host-pointer arguments
-    size_t staging_bytes = 0;
+    Staging own_staging;
+    Staging* stg = &own_staging;         // a batch member uses its batch's staging
+    Batch* owner = nullptr;              // batch whose arena holds buf[] (member views)
+    int member = -1;
+    // discrete adjoint workspace (allocated on first use)
+    float* adj_scratch = nullptr;        // float[kAdjPlanes][n]
+    double* adj_partials = nullptr;      // double[adj_blocks][kAdjSlots]
+    double* adj_out = nullptr;           // double[kAdjSlots]
+    float* adj_lam[2] = {nullptr, nullptr};
+    float* adj_ckpt = nullptr;           // checkpoints, float[cap][18][n]
+    size_t adj_ckpt_cap = 0;
+    float* adj_seg = nullptr;            // recomputed segment states, float[cap][18][n]
+    size_t adj_seg_cap = 0;
+    size_t adj_bytes = 0;
     int rows = 128;                      // rows per CTA of the chain kernel
     int64_t t = 0;
     int64_t launches = 0;
@@ -41,6 +64,51 @@ struct Ctx {
 
 struct cmrt_ctx {
     Ctx c;
+};
+
+namespace {
+
+// An ensemble of independent lattices stepped together by the persistent
+// batched kernel.  All members share one storage precision; their states
+// live in two arenas (A-B), member m at byte offset off[m] of each.
+struct Batch {
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;      // private stream on which graphs are recorded
+    int precision = 0;
+    bool vec = true;                     // every member has nx % 4 == 0
+    std::vector<cmrt_params> p;
+    std::vector<StepParams> sp;
+    std::vector<size_t> off;
+    size_t arena_bytes = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t t = 0;
+    int64_t launches = 0;
+    size_t dev_bytes = 0;
+    StepParams* d_params = nullptr;
+    size_t* d_off = nullptr;
+    unsigned* d_flags = nullptr;
+    unsigned* d_counters = nullptr;
+    cmrt::BatchItem* d_items = nullptr;
+    size_t items_cap = 0;
+    int nitems = 0;
+    int grid = 0;                        // persistent CTAs
+    int diag_every = 0;                  // smallest positive diag_every of the members
+    std::map<std::string, int> rows;     // size class -> rows per work item
+    int graph_steps = 32;                // steps per recorded graph (even), 0 = none
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};  // graphs starting from parity 0 / 1
+    std::vector<cmrt_ctx*> views;
+    Staging staging;
+    bool failed = false;
+    std::string err;
+};
+
+}  // namespace
+
+struct cmrt_batch {
+    Batch b;
 };
 
 namespace {
@@ -182,22 +250,21 @@ bool is_device_ptr(const void* ptr) {
 }
 
 cmrt_status ensure_staging(Ctx* c, size_t bytes) {
-    if (c->staging_bytes >= bytes) return CMRT_OK;
-    if (c->staging) {
+    Staging& st = *c->stg;
+    if (st.bytes >= bytes) return CMRT_OK;
+    if (st.ptr) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->staging);
-        c->dev_bytes -= c->staging_bytes;
-        c->staging = nullptr;
-        c->staging_bytes = 0;
+        cudaFree(st.ptr);
+        st.ptr = nullptr;
+        st.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&c->staging, bytes);
+    cudaError_t e = cudaMalloc(&st.ptr, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        c->staging = nullptr;
+        st.ptr = nullptr;
         return fail(c, CMRT_ENOMEM, "cudaMalloc of %zu staging bytes failed: %s", bytes, cudaGetErrorString(e));
     }
-    c->staging_bytes = bytes;
-    c->dev_bytes += bytes;
+    st.bytes = bytes;
     return CMRT_OK;
 }
 
@@ -210,7 +277,16 @@ Ctx* live(cmrt_ctx* h) {
         g_thread_error = "context has failed earlier: " + h->c.err;
         return nullptr;
     }
-    return &h->c;
+    Ctx* c = &h->c;
+    if (c->owner) {  // a member view follows its batch's time and buffer parity
+        if (c->owner->failed) {
+            g_thread_error = "batch has failed earlier: " + c->owner->err;
+            return nullptr;
+        }
+        c->cur = c->owner->cur;
+        c->t = c->owner->t;
+    }
+    return c;
 }
 
 cmrt_status set_device(Ctx* c) {
@@ -221,12 +297,23 @@ cmrt_status set_device(Ctx* c) {
 }
 
 void free_all(Ctx* c) {
-    for (void*& b : c->buf)
-        if (b) cudaFree(b), b = nullptr;
-    if (c->d_flag) cudaFree(c->d_flag), c->d_flag = nullptr;
+    if (!c->owner) {  // a member view borrows its state and flag from the batch
+        for (void*& b : c->buf)
+            if (b) cudaFree(b), b = nullptr;
+        if (c->d_flag) cudaFree(c->d_flag), c->d_flag = nullptr;
+    }
     if (c->d_partials) cudaFree(c->d_partials), c->d_partials = nullptr;
     if (c->d_diag) cudaFree(c->d_diag), c->d_diag = nullptr;
-    if (c->staging) cudaFree(c->staging), c->staging = nullptr;
+    if (c->own_staging.ptr) cudaFree(c->own_staging.ptr), c->own_staging.ptr = nullptr;
+    if (c->adj_scratch) cudaFree(c->adj_scratch), c->adj_scratch = nullptr;
+    if (c->adj_partials) cudaFree(c->adj_partials), c->adj_partials = nullptr;
+    if (c->adj_out) cudaFree(c->adj_out), c->adj_out = nullptr;
+    for (float*& l : c->adj_lam)
+        if (l) cudaFree(l), l = nullptr;
+    if (c->adj_ckpt) cudaFree(c->adj_ckpt), c->adj_ckpt = nullptr;
+    if (c->adj_seg) cudaFree(c->adj_seg), c->adj_seg = nullptr;
+    c->adj_bytes = 0;
+    c->adj_ckpt_cap = c->adj_seg_cap = 0;
 }
 
 cmrt_status check_flag(Ctx* c) {
@@ -234,6 +321,47 @@ cmrt_status check_flag(Ctx* c) {
     CK(c, cudaMemcpyAsync(&h, c->d_flag, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (h) return fail(c, CMRT_ENONFINITE, "non-finite density in the state before step %lld", (long long)c->t);
+    return CMRT_OK;
+}
+
+// Writes the state at t = 0 into c->buf[c->cur] (Eqs. equ_rhoN_def, equ_equ):
+// the equilibrium of the colour field rho_n0 and velocity u0 (host or device
+// pointers, NULL for -1 and 0).
+cmrt_status init_state(Ctx* c, const float* rho_n0, const float* u0) {
+    const cmrt_params* p = &c->p;
+    const size_t n = cells(*c);
+    // inputs: copy host arrays into staging (after an FP32 state area when the
+    // state is stored in 16 bits and has to be encoded from FP32)
+    const float* d_rn = rho_n0;
+    const float* d_u = u0;
+    const bool rn_host = rho_n0 && !is_device_ptr(rho_n0);
+    const bool u_host = u0 && !is_device_ptr(u0);
+    const bool packed = p->precision != 0;
+    const size_t in_off = packed ? 18 * n : 0;
+    if (rn_host || u_host || packed) {
+        if (ensure_staging(c, (in_off + ((rn_host || u_host) ? 3 * n : 0)) * sizeof(float)) != CMRT_OK)
+            return CMRT_ENOMEM;
+        if (rn_host) {
+            CK(c, cudaMemcpyAsync(c->stg->ptr + in_off, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            d_rn = c->stg->ptr + in_off;
+        }
+        if (u_host) {
+            CK(c, cudaMemcpyAsync(c->stg->ptr + in_off + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream));
+            d_u = c->stg->ptr + in_off + n;
+        }
+    }
+    float* post32 = packed ? c->stg->ptr : static_cast<float*>(c->buf[c->cur]);
+    CK(c, cmrt::launch_init_fp64(d_rn, d_u, p->nx, p->ny, p->wall_y, p->rho0_r, p->rho0_b, p->alpha_r, p->alpha_b,
+                                 post32, c->stream));
+    c->launches++;
+    if (packed) {
+        CK(c, cmrt::launch_encode(post32, c->sp, c->buf[c->cur], c->stream));
+        c->launches++;
+    }
+    // host buffers may be reused by the caller as soon as we return, and the
+    // staging area by the next call
+    if (rn_host || u_host || packed) CK(c, cudaStreamSynchronize(c->stream));
     return CMRT_OK;
 }
 
@@ -329,54 +457,9 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
         fail(c, CMRT_ECUDA, "cudaMemsetAsync failed");
         return bail(CMRT_ECUDA);
     }
-    // inputs: copy host arrays into staging (after an FP32 state area when the
-    // state is stored in 16 bits and has to be encoded from FP32)
-    const float* d_rn = rho_n0;
-    const float* d_u = u0;
-    const bool rn_host = rho_n0 && !is_device_ptr(rho_n0);
-    const bool u_host = u0 && !is_device_ptr(u0);
-    const bool packed = p->precision != 0;
-    const size_t in_off = packed ? 18 * n : 0;
-    if (rn_host || u_host || packed) {
-        if (ensure_staging(c, (in_off + ((rn_host || u_host) ? 3 * n : 0)) * sizeof(float)) != CMRT_OK)
-            return bail(CMRT_ENOMEM);
-        if (rn_host) {
-            if (cudaMemcpyAsync(c->staging + in_off, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess) {
-                fail(c, CMRT_ECUDA, "copy of rho_n0 failed");
-                return bail(CMRT_ECUDA);
-            }
-            d_rn = c->staging + in_off;
-        }
-        if (u_host) {
-            if (cudaMemcpyAsync(c->staging + in_off + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice,
-                                c->stream) != cudaSuccess) {
-                fail(c, CMRT_ECUDA, "copy of u0 failed");
-                return bail(CMRT_ECUDA);
-            }
-            d_u = c->staging + in_off + n;
-        }
-    }
-    float* post32 = packed ? c->staging : static_cast<float*>(c->buf[0]);
-    cudaError_t e = cmrt::launch_init_fp64(d_rn, d_u, p->nx, p->ny, p->wall_y, p->rho0_r, p->rho0_b, p->alpha_r,
-                                           p->alpha_b, post32, c->stream);
-    if (e == cudaSuccess && packed) {
-        c->launches++;
-        e = cmrt::launch_encode(post32, c->sp, c->buf[0], c->stream);
-    }
-    if (e != cudaSuccess) {
-        fail(c, CMRT_ECUDA, "init kernel launch failed: %s", cudaGetErrorString(e));
-        return bail(CMRT_ECUDA);
-    }
-    c->launches++;
-    if (rn_host || u_host || packed) {
-        // host buffers may be reused by the caller as soon as we return, and the
-        // staging area by the next call
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-            fail(c, CMRT_ECUDA, "stream synchronisation failed");
-            return bail(CMRT_ECUDA);
-        }
-    }
+    c->cur = 0;
+    st = init_state(c, rho_n0, u0);
+    if (st != CMRT_OK) return bail(st);
     c->cur = 0;
     c->t = 0;
     *out = h;
@@ -387,6 +470,7 @@ cmrt_status cmrt_step(cmrt_ctx* h, int64_t n) {
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (n < 0) return fail(c, CMRT_EINVAL, "n must be >= 0");
+    if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
     for (int64_t k = 0; k < n; ++k) {
         CK(c, cmrt::launch_step(c->buf[c->cur], c->buf[c->cur ^ 1], c->sp, c->rows, c->d_flag, c->stream));
@@ -413,7 +497,7 @@ cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, floa
     if (any_host && ensure_staging(c, 5 * n * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
     for (int k = 0; k < 5; ++k) {
         if (!outs[k]) dev[k] = nullptr;
-        else dev[k] = is_device_ptr(outs[k]) ? outs[k] : c->staging + k * n;
+        else dev[k] = is_device_ptr(outs[k]) ? outs[k] : c->stg->ptr + k * n;
     }
     CK(c, cmrt::launch_fields(c->buf[c->cur], c->sp, c->rows, cmrt::FieldOut{dev[0], dev[1], dev[2], dev[3], dev[4]},
                               c->stream));
@@ -462,11 +546,11 @@ cmrt_status cmrt_get_populations(cmrt_ctx* h, float* dst) {
     if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
     const float* post32 = static_cast<const float*>(c->buf[c->cur]);
     if (packed) {
-        CK(c, cmrt::launch_decode(c->buf[c->cur], c->sp, c->staging, c->stream));
+        CK(c, cmrt::launch_decode(c->buf[c->cur], c->sp, c->stg->ptr, c->stream));
         c->launches++;
-        post32 = c->staging;
+        post32 = c->stg->ptr;
     }
-    float* d = host ? c->staging + (packed ? n18 : 0) : dst;
+    float* d = host ? c->stg->ptr + (packed ? n18 : 0) : dst;
     CK(c, cmrt::launch_stream_out(post32, c->sp, d, c->stream));
     c->launches++;
     if (host) {
@@ -490,11 +574,11 @@ cmrt_status cmrt_set_populations(cmrt_ctx* h, const float* src) {
     const size_t need = (packed ? n18 : 0) + (host ? n18 : 0);
     if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
     if (host) {
-        float* hs = c->staging + (packed ? n18 : 0);
+        float* hs = c->stg->ptr + (packed ? n18 : 0);
         CK(c, cudaMemcpyAsync(hs, src, bytes, cudaMemcpyHostToDevice, c->stream));
         s = hs;
     }
-    float* post32 = packed ? c->staging : static_cast<float*>(c->buf[c->cur]);
+    float* post32 = packed ? c->stg->ptr : static_cast<float*>(c->buf[c->cur]);
     CK(c, cmrt::launch_unstream_in(s, c->sp, post32, c->stream));
     c->launches++;
     if (packed) {
@@ -512,14 +596,19 @@ cmrt_status cmrt_synchronize(cmrt_ctx* h) {
     return CMRT_OK;
 }
 
-int64_t cmrt_time(const cmrt_ctx* h) { return h ? h->c.t : -1; }
+int64_t cmrt_time(const cmrt_ctx* h) {
+    if (!h) return -1;
+    return h->c.owner ? h->c.owner->t : h->c.t;  // a member view follows its batch
+}
 
 int64_t cmrt_launch_count(const cmrt_ctx* h) { return h ? h->c.launches : -1; }
 
-size_t cmrt_device_bytes(const cmrt_ctx* h) { return h ? h->c.dev_bytes : 0; }
+size_t cmrt_device_bytes(const cmrt_ctx* h) {
+    return h ? h->c.dev_bytes + h->c.own_staging.bytes + h->c.adj_bytes : 0;
+}
 
 void cmrt_destroy(cmrt_ctx* h) {
-    if (!h) return;
+    if (!h || h->c.owner) return;  // member views are freed with their batch
     Ctx* c = &h->c;
     int cur = -1;
     if (cudaGetDevice(&cur) == cudaSuccess && cur != c->device) cudaSetDevice(c->device);
@@ -625,3 +714,789 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
     return CMRT_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched ensembles (cmrt_batch_*).
+//
+// Hundreds of independent lattices advance together: one persistent launch
+// per time step drains a work list of tiles (member, strip, row segment)
+// ordered longest first.  The rows of a tile are set per size class (nx, ny,
+// walls) by cmrt_batch_set_rows or by the autotuner, which times whole
+// batched launches that do not advance the state and keeps the best rows per
+// class (coordinate descent, results cached in a JSON file).  Steps are
+// replayed from CUDA graphs of graph_steps launches recorded once per buffer
+// parity.
+// ---------------------------------------------------------------------------
+namespace {
+
+cmrt_status bfail(Batch* b, cmrt_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) {
+        b->err = buf;
+        if (st == CMRT_ECUDA || st == CMRT_ENONFINITE) b->failed = true;
+    }
+    g_thread_error = buf;
+    return st;
+}
+
+#define BCK(b, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail((b), CMRT_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+std::string class_key(const cmrt_params& p) {
+    char k[64];
+    snprintf(k, sizeof k, "%dx%dw%d", p.nx, p.ny, p.wall_y);
+    return k;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Rows per work item before tuning: whole lattices up to 64 rows, else 64.
+int default_rows(const cmrt_params& p) { return std::min(64, std::max(1, p.ny)); }
+
+Batch* blive(cmrt_batch* h) {
+    if (!h) {
+        bfail(nullptr, CMRT_ESTATE, "NULL batch");
+        return nullptr;
+    }
+    if (h->b.failed) {
+        g_thread_error = "batch has failed earlier: " + h->b.err;
+        return nullptr;
+    }
+    return &h->b;
+}
+
+cmrt_status bset_device(Batch* b) {
+    int cur = -1;
+    BCK(b, cudaGetDevice(&cur));
+    if (cur != b->device) BCK(b, cudaSetDevice(b->device));
+    return CMRT_OK;
+}
+
+void drop_graphs(Batch* b) {
+    for (cudaGraphExec_t& e : b->exec)
+        if (e) cudaGraphExecDestroy(e), e = nullptr;
+}
+
+void free_batch(Batch* b) {
+    drop_graphs(b);
+    for (cmrt_ctx*& v : b->views) {
+        if (v) {
+            free_all(&v->c);
+            delete v;
+            v = nullptr;
+        }
+    }
+    for (void*& p : b->buf)
+        if (p) cudaFree(p), p = nullptr;
+    if (b->d_params) cudaFree(b->d_params), b->d_params = nullptr;
+    if (b->d_off) cudaFree(b->d_off), b->d_off = nullptr;
+    if (b->d_flags) cudaFree(b->d_flags), b->d_flags = nullptr;
+    if (b->d_counters) cudaFree(b->d_counters), b->d_counters = nullptr;
+    if (b->d_items) cudaFree(b->d_items), b->d_items = nullptr;
+    if (b->staging.ptr) cudaFree(b->staging.ptr), b->staging.ptr = nullptr;
+    if (b->capture) cudaStreamDestroy(b->capture), b->capture = nullptr;
+}
+
+// Work list for the current rows per class: every member cut into strips of
+// kTileX columns and segments of its class's rows, longest segments first,
+// and within equal lengths member by member, segment by segment, so that
+// neighbouring strips (which share halo columns) run close together in time.
+cmrt_status build_items(Batch* b) {
+    std::vector<cmrt::BatchItem> items;
+    for (int m = 0; m < b->n; ++m) {
+        const cmrt_params& p = b->p[m];
+        const int r = b->rows[class_key(p)];
+        const int strips = (p.nx + cmrt::kTileX - 1) / cmrt::kTileX;
+        for (int y0 = 0; y0 < p.ny; y0 += r)
+            for (int s = 0; s < strips; ++s)
+                items.push_back(cmrt::BatchItem{m, s * cmrt::kTileX, y0, std::min(r, p.ny - y0)});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const cmrt::BatchItem& a, const cmrt::BatchItem& c) { return a.rows > c.rows; });
+    // the kernels of earlier steps may still read the old list
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (items.size() > b->items_cap) {
+        if (b->d_items) {
+            cudaFree(b->d_items);
+            b->dev_bytes -= b->items_cap * sizeof(cmrt::BatchItem);
+            b->d_items = nullptr;
+            b->items_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&b->d_items, items.size() * sizeof(cmrt::BatchItem));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->d_items = nullptr;
+            return bfail(b, CMRT_ENOMEM, "cudaMalloc of the work list failed: %s", cudaGetErrorString(e));
+        }
+        b->items_cap = items.size();
+        b->dev_bytes += b->items_cap * sizeof(cmrt::BatchItem);
+    }
+    BCK(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(cmrt::BatchItem), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->nitems = static_cast<int>(items.size());
+    drop_graphs(b);  // they hold the old list length
+    return CMRT_OK;
+}
+
+cudaError_t batch_launch(Batch* b, int src_parity, cudaStream_t s) {
+    cmrt::BatchArgs A{b->d_items, b->nitems, b->d_params, b->d_off,
+                      static_cast<const char*>(b->buf[src_parity]), static_cast<char*>(b->buf[src_parity ^ 1]),
+                      b->d_flags, b->d_counters};
+    return cmrt::launch_batch(A, b->precision, b->vec, b->grid, s);
+}
+
+// Records graph_steps batched steps starting from buffer parity `parity`.
+cmrt_status build_graph(Batch* b, int parity) {
+    BCK(b, cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; ++k) e = batch_launch(b, (parity + k) & 1, b->capture);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, CMRT_ECUDA, "recording the step graph failed: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec[parity] = nullptr;
+        return bfail(b, CMRT_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+    }
+    return CMRT_OK;
+}
+
+cmrt_status check_batch_flags(Batch* b) {
+    std::vector<unsigned> h(b->n);
+    BCK(b, cudaMemcpyAsync(h.data(), b->d_flags, b->n * sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int m = 0; m < b->n; ++m)
+        if (h[m]) return bfail(b, CMRT_ENONFINITE, "member %d has a non-finite density before step %lld", m, (long long)b->t);
+    return CMRT_OK;
+}
+
+// ----- autotuner cache: a JSON array with one object per line -----
+std::string json_str(const std::string& line, const char* key) {
+    const std::string k = std::string("\"") + key + "\": \"";
+    const size_t a = line.find(k);
+    if (a == std::string::npos) return "";
+    const size_t b = line.find('"', a + k.size());
+    if (b == std::string::npos) return "";
+    return line.substr(a + k.size(), b - a - k.size());
+}
+
+std::string sanitize(std::string v) {
+    for (char& ch : v)
+        if (ch == '"' || ch == '\\' || static_cast<unsigned char>(ch) < 32) ch = '_';
+    return v;
+}
+
+std::vector<std::string> read_lines(const char* path) {
+    std::vector<std::string> out;
+    FILE* f = fopen(path, "r");
+    if (!f) return out;
+    char buf[8192];
+    while (fgets(buf, sizeof buf, f)) {
+        std::string l(buf);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        if (l.find("\"signature\"") != std::string::npos) {
+            if (!l.empty() && l.back() == ',') l.pop_back();
+            out.push_back(l);
+        }
+    }
+    fclose(f);
+    return out;
+}
+
+bool write_lines(const char* path, const std::vector<std::string>& lines) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fputs("[\n", f);
+    for (size_t i = 0; i < lines.size(); ++i) fprintf(f, "%s%s\n", lines[i].c_str(), i + 1 < lines.size() ? "," : "");
+    fputs("]\n", f);
+    const bool ok = fclose(f) == 0;
+    return ok && std::rename(tmp.c_str(), path) == 0;
+}
+
+// "64x64w0=32 128x128w0=64" <-> the rows map
+std::string rows_string(const std::map<std::string, int>& rows) {
+    std::string s;
+    for (const auto& kv : rows) s += (s.empty() ? "" : " ") + kv.first + "=" + std::to_string(kv.second);
+    return s;
+}
+
+bool parse_rows(const std::string& s, std::map<std::string, int>& rows) {
+    std::map<std::string, int> got;
+    size_t pos = 0;
+    while (pos < s.size()) {
+        size_t end = s.find(' ', pos);
+        if (end == std::string::npos) end = s.size();
+        const std::string tok = s.substr(pos, end - pos);
+        const size_t eq = tok.find('=');
+        if (eq == std::string::npos) return false;
+        const int r = std::atoi(tok.c_str() + eq + 1);
+        if (r < 1) return false;
+        got[tok.substr(0, eq)] = r;
+        pos = end + 1;
+    }
+    for (const auto& kv : rows)
+        if (!got.count(kv.first)) return false;
+    for (auto& kv : rows) kv.second = got[kv.first];
+    return true;
+}
+
+// Signature of what the tuned rows depend on: storage, vector path and the
+// multiset of size classes.
+std::string batch_signature(const Batch* b) {
+    std::map<std::string, int> count;
+    for (const cmrt_params& p : b->p) count[class_key(p)]++;
+    std::string s = "p" + std::to_string(b->precision) + " v" + std::to_string(b->vec ? 1 : 0);
+    for (const auto& kv : count) s += " " + kv.first + "*" + std::to_string(kv.second);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+cmrt_status cmrt_batch_init(int32_t n, const cmrt_params* params, const float* const* rho_n0, const float* const* u0,
+                            void* cuda_stream, cmrt_batch** out) {
+    if (!out) return bfail(nullptr, CMRT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !params) return bfail(nullptr, CMRT_EINVAL, "a batch needs n >= 1 members and their params");
+    for (int m = 0; m < n; ++m) {
+        cmrt_status st = validate(&params[m]);
+        if (st != CMRT_OK) return bfail(nullptr, st, "member %d: %s", m, g_thread_error.c_str());
+        if (params[m].precision != params[0].precision)
+            return bfail(nullptr, CMRT_EINVAL, "member %d: all members must share one storage precision", m);
+    }
+    cmrt_batch* h = new (std::nothrow) cmrt_batch;
+    if (!h) return bfail(nullptr, CMRT_ENOMEM, "host allocation of the batch failed");
+    Batch* b = &h->b;
+    auto bail = [&](cmrt_status s) {
+        g_thread_error = b->err.empty() ? g_thread_error : b->err;
+        free_batch(b);
+        delete h;
+        return s;
+    };
+    b->n = n;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->precision = params[0].precision;
+    b->p.assign(params, params + n);
+    b->views.assign(n, nullptr);
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        cudaGetLastError();
+        bfail(b, CMRT_ECUDA, "no CUDA device");
+        return bail(CMRT_ECUDA);
+    }
+    const size_t node = cmrt::state_node_bytes(b->precision);
+    for (int m = 0; m < n; ++m) {
+        b->sp.push_back(derive(params[m]));
+        b->vec = b->vec && (params[m].nx % 4) == 0;
+        b->off.push_back(b->arena_bytes);
+        const size_t bytes = static_cast<size_t>(params[m].nx) * params[m].ny * node;
+        b->arena_bytes += (bytes + 255) / 256 * 256;  // 256-byte aligned members
+        b->rows[class_key(params[m])] = default_rows(params[m]);
+        if (params[m].diag_every > 0 && (b->diag_every == 0 || params[m].diag_every < b->diag_every))
+            b->diag_every = params[m].diag_every;
+    }
+    auto dmalloc = [&](void** ptr, size_t bytes) {
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            bfail(b, CMRT_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            return false;
+        }
+        b->dev_bytes += bytes;
+        return true;
+    };
+    if (!dmalloc(&b->buf[0], b->arena_bytes) || !dmalloc(&b->buf[1], b->arena_bytes) ||
+        !dmalloc(reinterpret_cast<void**>(&b->d_params), n * sizeof(StepParams)) ||
+        !dmalloc(reinterpret_cast<void**>(&b->d_off), n * sizeof(size_t)) ||
+        !dmalloc(reinterpret_cast<void**>(&b->d_flags), n * sizeof(unsigned)) ||
+        !dmalloc(reinterpret_cast<void**>(&b->d_counters), 2 * sizeof(unsigned)))
+        return bail(CMRT_ENOMEM);
+    auto ck = [&](cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return true;
+        bfail(b, CMRT_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
+        return false;
+    };
+    if (!ck(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "cudaStreamCreateWithFlags") ||
+        !ck(cudaMemcpyAsync(b->d_params, b->sp.data(), n * sizeof(StepParams), cudaMemcpyHostToDevice, b->stream),
+            "copy of member parameters") ||
+        !ck(cudaMemcpyAsync(b->d_off, b->off.data(), n * sizeof(size_t), cudaMemcpyHostToDevice, b->stream),
+            "copy of member offsets") ||
+        !ck(cudaMemsetAsync(b->d_flags, 0, n * sizeof(unsigned), b->stream), "cudaMemsetAsync") ||
+        !ck(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned), b->stream), "cudaMemsetAsync"))
+        return bail(CMRT_ECUDA);
+    int per_sm = 0, sms = 0;
+    if (!ck(cmrt::prepare_batch(b->precision, b->vec, &per_sm), "setting up the batched kernel") ||
+        !ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "cudaDeviceGetAttribute"))
+        return bail(CMRT_ECUDA);
+    if (per_sm < 1) {
+        bfail(b, CMRT_ECUDA, "the batched kernel does not fit on an SM");
+        return bail(CMRT_ECUDA);
+    }
+    b->grid = per_sm * sms;
+    // initial states, member by member, through the single-lattice path
+    for (int m = 0; m < n; ++m) {
+        Ctx tmp;
+        tmp.p = params[m];
+        tmp.sp = b->sp[m];
+        tmp.device = b->device;
+        tmp.stream = b->stream;
+        tmp.buf[0] = static_cast<char*>(b->buf[0]) + b->off[m];
+        tmp.buf[1] = static_cast<char*>(b->buf[1]) + b->off[m];
+        tmp.cur = 0;
+        tmp.stg = &b->staging;
+        tmp.owner = b;
+        cmrt_status st = init_state(&tmp, rho_n0 ? rho_n0[m] : nullptr, u0 ? u0[m] : nullptr);
+        b->launches += tmp.launches;
+        if (st != CMRT_OK) {
+            bfail(b, st, "member %d: %s", m, tmp.err.c_str());
+            return bail(st);
+        }
+    }
+    if (build_items(b) != CMRT_OK) return bail(CMRT_ECUDA);
+    *out = h;
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_step(cmrt_batch* h, int64_t n) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    if (n < 0) return bfail(b, CMRT_EINVAL, "n must be >= 0");
+    if (bset_device(b) != CMRT_OK) return CMRT_ECUDA;
+    int64_t left = n;
+    while (left > 0) {
+        int64_t chunk = left;
+        if (b->diag_every > 0) chunk = std::min<int64_t>(chunk, b->diag_every - b->t % b->diag_every);
+        left -= chunk;
+        while (b->graph_steps > 0 && chunk >= b->graph_steps) {
+            if (!b->exec[b->cur] && build_graph(b, b->cur) != CMRT_OK) return CMRT_ECUDA;
+            BCK(b, cudaGraphLaunch(b->exec[b->cur], b->stream));
+            b->t += b->graph_steps;  // an even count: the parity is unchanged
+            b->launches += b->graph_steps;
+            chunk -= b->graph_steps;
+        }
+        for (; chunk > 0; --chunk) {
+            BCK(b, batch_launch(b, b->cur, b->stream));
+            b->cur ^= 1;
+            b->t++;
+            b->launches++;
+        }
+        if (b->diag_every > 0 && b->t % b->diag_every == 0) {
+            cmrt_status st = check_batch_flags(b);
+            if (st != CMRT_OK) return st;
+        }
+    }
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_set_rows(cmrt_batch* h, int32_t nx, int32_t ny, int32_t wall_y, int32_t rows) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    cmrt_params k{};
+    k.nx = nx;
+    k.ny = ny;
+    k.wall_y = wall_y;
+    auto it = b->rows.find(class_key(k));
+    if (it == b->rows.end()) return bfail(b, CMRT_EINVAL, "no member of size %d x %d with wall_y %d", nx, ny, wall_y);
+    if (rows < 1) return bfail(b, CMRT_EINVAL, "rows must be >= 1");
+    if (bset_device(b) != CMRT_OK) return CMRT_ECUDA;
+    it->second = rows;
+    return build_items(b);
+}
+
+int32_t cmrt_batch_get_rows(const cmrt_batch* h, int32_t nx, int32_t ny, int32_t wall_y) {
+    if (!h) return -1;
+    cmrt_params k{};
+    k.nx = nx;
+    k.ny = ny;
+    k.wall_y = wall_y;
+    auto it = h->b.rows.find(class_key(k));
+    return it == h->b.rows.end() ? -1 : it->second;
+}
+
+cmrt_status cmrt_batch_set_graph_steps(cmrt_batch* h, int32_t steps) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    if (steps < 0 || steps % 2 != 0) return bfail(b, CMRT_EINVAL, "graph steps must be 0 or a positive even number");
+    if (bset_device(b) != CMRT_OK) return CMRT_ECUDA;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    drop_graphs(b);
+    b->graph_steps = steps;
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_tune(cmrt_batch* h, const char* cache_path, int32_t flags, double* us_per_step) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    if (bset_device(b) != CMRT_OK) return CMRT_ECUDA;
+    cudaDeviceProp prop{};
+    BCK(b, cudaGetDeviceProperties(&prop, b->device));
+    const std::string device = sanitize(prop.name);
+    const std::string sig = batch_signature(b);
+    std::vector<std::string> lines;
+    if (cache_path) lines = read_lines(cache_path);
+    if (cache_path && !(flags & CMRT_TUNE_FORCE)) {
+        for (const std::string& l : lines) {
+            if (json_str(l, "device") != device || json_str(l, "signature") != sig) continue;
+            const size_t a = l.find("\"sms\": ");
+            if (a == std::string::npos || std::atoi(l.c_str() + a + 7) != prop.multiProcessorCount) continue;
+            std::map<std::string, int> rows = b->rows;
+            if (!parse_rows(json_str(l, "rows"), rows)) continue;
+            b->rows = rows;
+            if (us_per_step) {
+                const size_t u = l.find("\"us_per_step\": ");
+                *us_per_step = u == std::string::npos ? 0.0 : std::atof(l.c_str() + u + 15);
+            }
+            return build_items(b);
+        }
+    }
+    // Time whole batched launches from the current state into the other
+    // buffer: the state does not advance, so tuning leaves results unchanged.
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    auto time_us = [&](double* us) -> cmrt_status {
+        cmrt_status st = build_items(b);
+        if (st != CMRT_OK) return st;
+        constexpr int kWarm = 2, kReps = 5;
+        for (int k = 0; k < kWarm; ++k) BCK(b, batch_launch(b, b->cur, b->stream));
+        BCK(b, cudaEventRecord(e0, b->stream));
+        for (int k = 0; k < kReps; ++k) BCK(b, batch_launch(b, b->cur, b->stream));
+        BCK(b, cudaEventRecord(e1, b->stream));
+        BCK(b, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+        b->launches += kWarm + kReps;
+        *us = 1000.0 * ms / kReps;
+        return CMRT_OK;
+    };
+    cmrt_status st = CMRT_OK;
+    double best = 0.0;
+    st = time_us(&best);
+    for (int pass = 0; pass < 2 && st == CMRT_OK; ++pass) {
+        for (auto& kv : b->rows) {
+            const int ny = std::atoi(kv.first.c_str() + kv.first.find('x') + 1);
+            const int keep = kv.second;
+            int best_r = keep;
+            for (int r = 8; r <= 512 && st == CMRT_OK; r *= 2) {
+                const int rr = std::min(r, ny);
+                if (rr == keep) continue;
+                kv.second = rr;
+                double us = 0.0;
+                st = time_us(&us);
+                if (st == CMRT_OK && us < best) {
+                    best = us;
+                    best_r = rr;
+                }
+                if (r >= ny) break;
+            }
+            kv.second = best_r;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CMRT_OK) return st;
+    st = build_items(b);
+    if (st != CMRT_OK) return st;
+    if (us_per_step) *us_per_step = best;
+    if (cache_path) {
+        char line[4096];
+        snprintf(line, sizeof line,
+                 "{\"device\": \"%s\", \"sms\": %d, \"signature\": \"%s\", \"rows\": \"%s\", \"us_per_step\": %.1f}",
+                 device.c_str(), prop.multiProcessorCount, sig.c_str(), rows_string(b->rows).c_str(), best);
+        std::vector<std::string> keep;
+        for (const std::string& l : lines)
+            if (!(json_str(l, "device") == device && json_str(l, "signature") == sig)) keep.push_back(l);
+        keep.push_back(line);
+        if (!write_lines(cache_path, keep)) return bfail(b, CMRT_EINVAL, "cannot write the tuning cache %s", cache_path);
+    }
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_member(cmrt_batch* h, int32_t k, cmrt_ctx** view) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    if (!view) return bfail(b, CMRT_EINVAL, "view is NULL");
+    *view = nullptr;
+    if (k < 0 || k >= b->n) return bfail(b, CMRT_EINVAL, "member %d out of range [0, %d)", k, b->n);
+    if (!b->views[k]) {
+        if (bset_device(b) != CMRT_OK) return CMRT_ECUDA;
+        cmrt_ctx* v = new (std::nothrow) cmrt_ctx;
+        if (!v) return bfail(b, CMRT_ENOMEM, "host allocation of a member view failed");
+        Ctx* c = &v->c;
+        c->p = b->p[k];
+        c->sp = b->sp[k];
+        c->device = b->device;
+        c->stream = b->stream;
+        c->buf[0] = static_cast<char*>(b->buf[0]) + b->off[k];
+        c->buf[1] = static_cast<char*>(b->buf[1]) + b->off[k];
+        c->d_flag = b->d_flags + k;
+        c->stg = &b->staging;
+        c->owner = b;
+        c->member = k;
+        int sms = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        c->rows = cmrt::chain_rows(c->p.nx, c->p.ny, sms, c->p.precision);
+        const dim3 g = cmrt::chain_grid(c->p.nx, c->p.ny, c->rows);
+        c->n_partials = static_cast<int>(g.x * g.y);
+        if (cudaMalloc(&c->d_partials, sizeof(double) * cmrt::kDiagSlots * c->n_partials) != cudaSuccess ||
+            cudaMalloc(&c->d_diag, sizeof(double) * cmrt::kDiagSlots) != cudaSuccess) {
+            cudaGetLastError();
+            free_all(c);
+            delete v;
+            return bfail(b, CMRT_ENOMEM, "cudaMalloc of a member view's diagnostics buffers failed");
+        }
+        c->dev_bytes = sizeof(double) * cmrt::kDiagSlots * (c->n_partials + 1);
+        b->dev_bytes += c->dev_bytes;
+        b->views[k] = v;
+    }
+    *view = b->views[k];
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_diagnostics(cmrt_batch* h, double* out) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    if (!out) return bfail(b, CMRT_EINVAL, "out is NULL");
+    for (int m = 0; m < b->n; ++m) {
+        cmrt_ctx* v = nullptr;
+        cmrt_status st = cmrt_batch_member(h, m, &v);
+        if (st != CMRT_OK) return st;
+        st = cmrt_diagnostics(v, out + 6 * static_cast<size_t>(m));
+        b->launches += 2;
+        if (st == CMRT_ENONFINITE) return bfail(b, st, "member %d: %s", m, v->c.err.c_str());
+        if (st != CMRT_OK) return bfail(b, st, "member %d: %s", m, g_thread_error.c_str());
+    }
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_batch_synchronize(cmrt_batch* h) {
+    Batch* b = blive(h);
+    if (!b) return CMRT_ESTATE;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return CMRT_OK;
+}
+
+int32_t cmrt_batch_size(const cmrt_batch* h) { return h ? h->b.n : -1; }
+
+int64_t cmrt_batch_time(const cmrt_batch* h) { return h ? h->b.t : -1; }
+
+int64_t cmrt_batch_launch_count(const cmrt_batch* h) { return h ? h->b.launches : -1; }
+
+int64_t cmrt_batch_work_items(const cmrt_batch* h) { return h ? h->b.nitems : -1; }
+
+size_t cmrt_batch_device_bytes(const cmrt_batch* h) { return h ? h->b.dev_bytes + h->b.staging.bytes : 0; }
+
+void cmrt_batch_destroy(cmrt_batch* h) {
+    if (!h) return;
+    Batch* b = &h->b;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != b->device) cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    cudaGetLastError();
+    if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+    delete h;
+}
+
+const char* cmrt_batch_last_error(const cmrt_batch* h) {
+    if (h) return h->b.err.c_str();
+    return g_thread_error.c_str();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint (cmrt_step_vjp, cmrt_adjoint).
+// ---------------------------------------------------------------------------
+namespace {
+
+// Grows the adjoint workspace: scratch planes, partial sums, two adjoint
+// states, `ckpt` checkpoint states and `seg` recomputed segment states.
+cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
+    const size_t n = cells(*c);
+    const size_t state = 18 * n * sizeof(float);
+    auto grow = [&](void** ptr, size_t bytes) -> cmrt_status {
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return fail(c, CMRT_ENOMEM, "cudaMalloc of %zu adjoint bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
+        c->adj_bytes += bytes;
+        return CMRT_OK;
+    };
+    cmrt_status st = CMRT_OK;
+    if (!c->adj_scratch) {
+        const size_t nb = static_cast<size_t>(cmrt::adj_blocks(c->p.nx, c->p.ny));
+        if ((st = grow(reinterpret_cast<void**>(&c->adj_scratch), cmrt::kAdjPlanes * n * sizeof(float))) ||
+            (st = grow(reinterpret_cast<void**>(&c->adj_partials), nb * cmrt::kAdjSlots * sizeof(double))) ||
+            (st = grow(reinterpret_cast<void**>(&c->adj_out), cmrt::kAdjSlots * sizeof(double))) ||
+            (st = grow(reinterpret_cast<void**>(&c->adj_lam[0]), state)) ||
+            (st = grow(reinterpret_cast<void**>(&c->adj_lam[1]), state)))
+            return st;
+    }
+    if (ckpt > c->adj_ckpt_cap) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->adj_ckpt) cudaFree(c->adj_ckpt), c->adj_ckpt = nullptr, c->adj_bytes -= c->adj_ckpt_cap * state;
+        c->adj_ckpt_cap = 0;
+        if ((st = grow(reinterpret_cast<void**>(&c->adj_ckpt), ckpt * state))) return st;
+        c->adj_ckpt_cap = ckpt;
+    }
+    if (seg > c->adj_seg_cap) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->adj_seg) cudaFree(c->adj_seg), c->adj_seg = nullptr, c->adj_bytes -= c->adj_seg_cap * state;
+        c->adj_seg_cap = 0;
+        if ((st = grow(reinterpret_cast<void**>(&c->adj_seg), seg * state))) return st;
+        c->adj_seg_cap = seg;
+    }
+    return CMRT_OK;
+}
+
+// Reduces the partial sums into out[kAdjSlots] on the host (synchronises).
+cmrt_status adj_collect(Ctx* c, double* out) {
+    CK(c, cmrt::launch_adjoint_reduce(c->adj_partials, cmrt::adj_blocks(c->p.nx, c->p.ny), c->adj_out, c->stream));
+    c->launches++;
+    CK(c, cudaMemcpyAsync(out, c->adj_out, cmrt::kAdjSlots * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return CMRT_OK;
+}
+
+cmrt_status adj_zero(Ctx* c) {
+    CK(c, cudaMemsetAsync(c->adj_partials, 0,
+                          static_cast<size_t>(cmrt::adj_blocks(c->p.nx, c->p.ny)) * cmrt::kAdjSlots * sizeof(double),
+                          c->stream));
+    return CMRT_OK;
+}
+
+}  // namespace
+
+extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* lam, double grad_params[6]) {
+    Ctx* c = live(h);
+    if (!c) return CMRT_ESTATE;
+    if (!lam_next || !lam) return fail(c, CMRT_EINVAL, "lam_next and lam must not be NULL");
+    if (c->p.precision != 0) return fail(c, CMRT_EINVAL, "the adjoint needs FP32 storage (precision 0)");
+    if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
+    cmrt_status st = ensure_adj(c, 0, 0);
+    if (st != CMRT_OK) return st;
+    const size_t n18 = cells(*c) * 18;
+    const float* src = lam_next;
+    if (!is_device_ptr(lam_next)) {
+        CK(c, cudaMemcpyAsync(c->adj_lam[1], lam_next, n18 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        src = c->adj_lam[1];
+    }
+    // adjoint of P_t: the transpose of the gather f(t+1) = gather(P_t), a permutation
+    CK(c, cmrt::launch_unstream_in(src, c->sp, c->adj_lam[0], c->stream));
+    if ((st = adj_zero(c)) != CMRT_OK) return st;
+    const bool host = !is_device_ptr(lam);
+    float* dst = host ? c->adj_lam[1] : lam;
+    CK(c, cmrt::launch_adjoint_step_pre(static_cast<const float*>(c->buf[c->cur]), c->adj_lam[0], c->sp,
+                                        c->adj_scratch, c->adj_partials, dst, c->stream));
+    c->launches += 1 + cmrt::adj_launches_per_step(c->sp);
+    if (host) CK(c, cudaMemcpyAsync(lam, dst, n18 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    double out[cmrt::kAdjSlots];
+    if ((st = adj_collect(c, out)) != CMRT_OK) return st;
+    if (grad_params)
+        for (int k = 0; k < 6; ++k) grad_params[k] += out[k];
+    return CMRT_OK;
+}
+
+extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_every, const float* target, double* J,
+                                    double grad_params[6], float* grad_rho_n0) {
+    Ctx* c = live(h);
+    if (!c) return CMRT_ESTATE;
+    if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);
+    if (nsteps < 1 || ckpt_every < 1) return fail(c, CMRT_EINVAL, "nsteps and ckpt_every must be >= 1");
+    if (!target) return fail(c, CMRT_EINVAL, "target is NULL");
+    if (c->p.precision != 0) return fail(c, CMRT_EINVAL, "the adjoint needs FP32 storage (precision 0)");
+    if (grad_rho_n0 && c->t != 0)
+        return fail(c, CMRT_EINVAL, "grad_rho_n0 needs the initial state (time 0, now %lld)", (long long)c->t);
+    if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
+    const int64_t K = ckpt_every;
+    const size_t nck = static_cast<size_t>((nsteps + K - 1) / K);
+    const size_t seg = static_cast<size_t>(std::min<int64_t>(K, nsteps) - 1);
+    cmrt_status st = ensure_adj(c, nck, seg > 0 ? seg : 1);
+    if (st != CMRT_OK) return st;
+    const size_t n = cells(*c), n18 = 18 * n;
+    const size_t state = n18 * sizeof(float);
+    const float* d_target = target;
+    if (!is_device_ptr(target)) {
+        if (ensure_staging(c, n * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+        CK(c, cudaMemcpyAsync(c->stg->ptr, target, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        d_target = c->stg->ptr;
+    }
+    if ((st = adj_zero(c)) != CMRT_OK) return st;
+    // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
+    CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
+    for (int64_t t = 0; t < nsteps; ++t) {
+        CK(c, cmrt::launch_step(c->buf[c->cur], c->buf[c->cur ^ 1], c->sp, c->rows, c->d_flag, c->stream));
+        c->launches++;
+        c->cur ^= 1;
+        c->t++;
+        if ((t + 1) % K == 0 && t + 1 < nsteps)
+            CK(c, cudaMemcpyAsync(c->adj_ckpt + static_cast<size_t>((t + 1) / K) * n18, c->buf[c->cur], state,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // objective and its adjoint
+    int a = 0;
+    CK(c, cmrt::launch_adjoint_seed(static_cast<const float*>(c->buf[c->cur]), d_target, c->sp, c->adj_scratch,
+                                    c->adj_partials, c->adj_lam[a], c->stream));
+    c->launches += 2;
+    // segments in reverse: recompute the states from the checkpoint, then reverse them
+    for (int64_t k = static_cast<int64_t>(nck) - 1; k >= 0; --k) {
+        const int64_t s0 = k * K, s1 = std::min(s0 + K, nsteps);
+        const float* ck = c->adj_ckpt + static_cast<size_t>(k) * n18;
+        auto state_of = [&](int64_t j) { return j == 0 ? ck : c->adj_seg + static_cast<size_t>(j - 1) * n18; };
+        for (int64_t j = 1; j < s1 - s0; ++j) {
+            CK(c, cmrt::launch_step(state_of(j - 1), c->adj_seg + static_cast<size_t>(j - 1) * n18, c->sp, c->rows,
+                                    c->d_flag, c->stream));
+            c->launches++;
+        }
+        for (int64_t t = s1 - 1; t >= s0; --t) {
+            CK(c, cmrt::launch_adjoint_step(state_of(t - s0), c->adj_lam[a], c->sp, c->adj_scratch, c->adj_partials,
+                                            c->adj_lam[a ^ 1], c->stream));
+            c->launches += cmrt::adj_launches_per_step(c->sp);
+            a ^= 1;
+        }
+    }
+    if (grad_rho_n0) {
+        // f(0) and dJ/df(0): the gather of P_{-1} and of its adjoint (a permutation)
+        float* pre0 = c->adj_lam[a ^ 1];
+        float* lam0 = c->adj_scratch;  // 18 of its planes
+        CK(c, cmrt::launch_stream_out(c->adj_ckpt, c->sp, pre0, c->stream));
+        CK(c, cmrt::launch_stream_out(c->adj_lam[a], c->sp, lam0, c->stream));
+        const bool host = !is_device_ptr(grad_rho_n0);
+        float* g = grad_rho_n0;
+        if (host) {
+            if (ensure_staging(c, 2 * n * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+            g = c->stg->ptr + n;
+        }
+        CK(c, cmrt::launch_adjoint_init(pre0, lam0, c->sp, g, c->stream));
+        c->launches += 3;
+        if (host) CK(c, cudaMemcpyAsync(grad_rho_n0, g, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
+    double out[cmrt::kAdjSlots];
+    if ((st = adj_collect(c, out)) != CMRT_OK) return st;
+    if (J) *J = out[6];
+    if (grad_params)
+        for (int k = 0; k < 6; ++k) grad_params[k] = out[k];
+    return check_flag(c);
+}

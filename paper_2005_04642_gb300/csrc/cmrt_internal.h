@@ -77,6 +77,52 @@ cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int 
 // Reduces nblocks partial rows into out[kDiagSlots] (one CTA).
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s);
 
+// Batched ensembles: one work item is the strip [x0, x0 + kTileX) of rows
+// [y0, y0 + rows) of lattice `member`.
+struct BatchItem {
+    int member, x0, y0, rows;
+};
+
+// Arguments of one persistent batched launch (all pointers are device memory).
+struct BatchArgs {
+    const BatchItem* items;     // work list, in the order the CTAs take it
+    int nitems;
+    const StepParams* params;   // [members]
+    const size_t* offsets;      // [members] byte offset of a member's state in src and dst
+    const char* src;            // post-collision states P_{t-1} of all members
+    char* dst;                  // receives P_t
+    unsigned* flags;            // [members] non-finite flags
+    unsigned* counters;         // [2] next item, CTAs finished; zero between launches
+};
+
+// Sets up the batched kernel for a storage precision on the current device
+// and reports how many of its CTAs fit on one SM.
+cudaError_t prepare_batch(int precision, bool vec, int* ctas_per_sm);
+// One step of every member of a batch: `grid` persistent CTAs drain the work list.
+cudaError_t launch_batch(const BatchArgs& A, int precision, bool vec, int grid, cudaStream_t s);
+
+// Discrete adjoint (cmrt_adjoint.cu), FP32 storage.  scratch: float[kAdjPlanes][ny][nx];
+// partials: double[adj_blocks][kAdjSlots], accumulated by every launch (zero it
+// before the first): slots 0..5 = dJ/d(sigma, beta, lambda3_r, lambda3_b,
+// g_acc_x, g_acc_y), slot 6 = J.
+constexpr int kAdjPlanes = 38;
+constexpr int kAdjSlots = 8;
+int adj_blocks(int nx, int ny);
+int adj_launches_per_step(const StepParams& P);
+// lam_post: adjoint of P_t; post: P_{t-1}; writes the adjoint of P_{t-1} into lam_prev
+cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
+                                double* partials, float* lam_prev, cudaStream_t s);
+// same, but writes dJ/df(t) (pre-collision, float[2][9][ny][nx]) into lam_pre
+cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
+                                    double* partials, float* lam_pre, cudaStream_t s);
+// J of f(T) = gather(post) against target, and the adjoint of post (P_{T-1}) in lam_post
+cudaError_t launch_adjoint_seed(const float* post, const float* target, const StepParams& P, float* scratch,
+                                double* partials, float* lam_post, cudaStream_t s);
+// dJ/drho^N_0 from the initial pre-collision state and its adjoint
+cudaError_t launch_adjoint_init(const float* pre0, const float* lam_pre0, const StepParams& P, float* grad_rho_n0,
+                                cudaStream_t s);
+cudaError_t launch_adjoint_reduce(const double* partials, int nblocks, double* out, cudaStream_t s);
+
 // 16-bit storage: FP32 post-collision planes float[18][ny][nx] <-> the
 // deviation layout of P.precision (see cmrt_step.cu).
 cudaError_t launch_encode(const float* post32, const StepParams& P, void* state, cudaStream_t s);

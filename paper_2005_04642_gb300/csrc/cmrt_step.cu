@@ -21,7 +21,7 @@
 // with 16-byte cp.async copies, two rows ahead of use.  Each iteration runs
 // a wavefront of four stages on consecutive rows, each stage reading only
 // what the previous one left in shared memory:
-//   A (row s-1)  gather f, colour moments, rho^N, Phi'          (tile + 3)
+//   A (row s-1)  gather f, colour moments and fractions, Phi'   (tile + 3)
 //   B (row s-2)  grad rho^N and n-hat with the compact stencil   (tile + 2)
 //   C (row s-3)  K = div n-hat, force G, force-adjusted u        (tile + 1)
 //   D (row s-4)  grad Phi', div u, C_ab, MRT collision in moment
@@ -113,7 +113,7 @@ __device__ __forceinline__ void segregation(float sx, float sy, float (&seg)[9])
 // 32-bit: 18 FP32 planes.
 struct LayoutF32 {
     static constexpr int kSlotBytes = kPlanes * kWin * 4;
-    static constexpr bool kSplitA = false;  // ring A keeps rho^N for stage D
+    static constexpr bool kSplitA = false;  // ring A keeps the colour fractions for stage D
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
     static constexpr size_t node_bytes() { return kPlanes * 4; }
@@ -326,10 +326,10 @@ using LayoutB16 = Layout16<__nv_bfloat162>;
 template <class L>
 struct Geometry {
     static constexpr int kPopBytes = kRing * L::kSlotBytes;
-    // ring A: without kSplitA, rho^N, Phi', rho, j_x, j_y over 8 rows; with it,
-    // Phi' over 8 rows (ring Q) and rho^N, rho, j_x, j_y over 4 rows
+    // ring A: without kSplitA, chi_R, chi_B, Phi', rho, j_x, j_y over 8 rows;
+    // with it, Phi' over 8 rows (ring Q) and chi_R, chi_B, rho, j_x, j_y over 4 rows
     static constexpr int kQFloats = L::kSplitA ? 8 * kWin : 0;
-    static constexpr int kAFloats = L::kSplitA ? 4 * 4 * kWin : 8 * 5 * kWin;
+    static constexpr int kAFloats = L::kSplitA ? 4 * 5 * kWin : 8 * 6 * kWin;
     static constexpr int kBytes = kPopBytes + 4 * (kQFloats + kAFloats + kBFloats + kCFloats);
 };
 
@@ -341,21 +341,25 @@ struct Rings {
     float* b;
     float* c;
     __device__ __forceinline__ const char* slot(int row) const { return pop + (row & (kRing - 1)) * L::kSlotBytes; }
-    // ring A fields
-    __device__ __forceinline__ float* rhoN(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 0) * kWin : a + ((row & 7) * 5 + 0) * kWin;
+    // ring A fields: the colour fractions chi_R = a / (a + b), chi_B = b / (a + b)
+    // (a = rho_R / rho0_r, b = rho_B / rho0_b; rho^N = chi_R - chi_B, Eq. equ_rhoN_def)
+    __device__ __forceinline__ float* chiR(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 5 + 0) * kWin : a + ((row & 7) * 6 + 0) * kWin;
+    }
+    __device__ __forceinline__ float* chiB(int row) const {
+        return L::kSplitA ? a + ((row & 3) * 5 + 4) * kWin : a + ((row & 7) * 6 + 5) * kWin;
     }
     __device__ __forceinline__ float* phip(int row) const {
-        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 5 + 1) * kWin;
+        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 6 + 1) * kWin;
     }
     __device__ __forceinline__ float* rho(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 1) * kWin : a + ((row & 7) * 5 + 2) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 5 + 1) * kWin : a + ((row & 7) * 6 + 2) * kWin;
     }
     __device__ __forceinline__ float* jx(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 2) * kWin : a + ((row & 7) * 5 + 3) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 5 + 2) * kWin : a + ((row & 7) * 6 + 3) * kWin;
     }
     __device__ __forceinline__ float* jy(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 3) * kWin : a + ((row & 7) * 5 + 4) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 5 + 3) * kWin : a + ((row & 7) * 6 + 4) * kWin;
     }
     __device__ __forceinline__ float* B(int row, int f) const { return b + (((row & 3) * kBF) + f) * kWin; }
     __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
@@ -456,19 +460,26 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
                                  (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
                 const float a = rr * P.inv_rho0_r;
                 const float b = rb * P.inv_rho0_b;
-                const float rn = (a - b) * rcp(a + b);                 // Eq. equ_rhoN_def
+                // colour fractions: rho^N = chi_R - chi_B (Eq. equ_rhoN_def); kept
+                // apart so that the smaller one carries the gradient of a nearly
+                // pure region without the FP32 cancellation of rho^N near +-1
+                const float inv_ab = rcp(a + b);
+                const float chr = a * inv_ab, chb = b * inv_ab;
                 const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
-                R.rhoN(ya)[t] = rn;
+                R.chiR(ya)[t] = chr;
+                R.chiB(ya)[t] = chb;
                 R.phip(ya)[t] = phip;
                 R.rho(ya)[t] = rr + rb;
                 R.jx(ya)[t] = jx;
                 R.jy(ya)[t] = jy;
                 if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
-                    R.rhoN(-1)[t] = rn;
+                    R.chiR(-1)[t] = chr;
+                    R.chiB(-1)[t] = chb;
                     R.phip(-1)[t] = phip;
                 }
                 if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
-                    R.rhoN(ny)[t] = rn;
+                    R.chiR(ny)[t] = chr;
+                    R.chiB(ny)[t] = chb;
                     R.phip(ny)[t] = phip;
                 }
             }
@@ -479,9 +490,13 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
         {
             const int yb = s - 2;
             if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-                auto rn_row = [&](int r) { return R.rhoN(r); };
-                const float gx = ddx_at(rn_row, yb, t);
-                const float gy = ddy_at(rn_row, yb, t);
+                // grad rho^N = 2 grad chi_R = -2 grad chi_B (the stencil weights sum
+                // to zero), taken on the fraction that is the smaller at this node
+                const bool red_minor = R.chiR(yb)[t] < R.chiB(yb)[t];
+                auto ch_row = [&](int r) { return red_minor ? R.chiR(r) : R.chiB(r); };
+                const float sgn = red_minor ? 2.0f : -2.0f;
+                const float gx = sgn * ddx_at(ch_row, yb, t);
+                const float gy = sgn * ddy_at(ch_row, yb, t);
                 // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
                 const float mag2 = fmaf(gx, gx, gy * gy);
                 const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
@@ -575,7 +590,7 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
                             const float ra = rr * P.inv_rho0_r, ba = rb * P.inv_rho0_b;
                             rn = (ra - ba) * rcp(ra + ba);
                         } else {
-                            rn = R.rhoN(yd)[t];
+                            rn = fmaf(2.0f, R.chiR(yd)[t], -1.0f);  // only sets nu: no cancellation concern
                         }
                         nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
                     } else {
@@ -715,6 +730,74 @@ __global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>())
     }
 }
 
+// Batched ensemble: a persistent kernel over a work list of tiles of many
+// independent lattices.  Each CTA takes the next item (member, strip, row
+// segment) from a global counter until the list is exhausted; every item is
+// the same four-stage row pipeline as k_chain, run with that member's own
+// parameters and buffers.  No CTA waits on another: an atomicAdd hands out
+// the items, and the last CTA to leave resets the counters for the next
+// launch.
+template <class L, bool VEC>
+__global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>()) k_batch(const BatchArgs A) {
+    using G = Geometry<L>;
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_item;
+    Rings<L> R;
+    R.pop = smem;
+    R.q = reinterpret_cast<float*>(smem + G::kPopBytes);
+    R.a = R.q + G::kQFloats;
+    R.b = R.a + G::kAFloats;
+    R.c = R.b + kBFloats;
+    const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    for (;;) {
+        __syncthreads();  // the previous item is done with the rings and s_item
+        if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(&A.counters[0], 1u));
+        __syncthreads();
+        const int it = s_item;
+        if (it >= A.nitems) break;
+        const BatchItem w = A.items[it];
+        const StepParams P = A.params[w.member];  // a register copy: stores cannot alias it
+        const size_t off = A.offsets[w.member];
+        DiagAcc acc;
+        if (P.wall_y)
+            chain_tile<L, VEC, true, Pass::Step, false>(R, pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0, w.rows,
+                                                        FieldOut{}, A.flags + w.member, acc);
+        else
+            chain_tile<L, VEC, false, Pass::Step, false>(R, pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0,
+                                                         w.rows, FieldOut{}, A.flags + w.member, acc);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's last counter access precedes its exit count
+        const unsigned done = atomicAdd(&A.counters[1], 1u);
+        if (done == gridDim.x - 1) {
+            A.counters[0] = 0u;
+            A.counters[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <class L, bool VEC>
+cudaError_t batch_configure(int dev, int* ctas_per_sm) {
+    static unsigned long long configured = 0;
+    const unsigned long long bit = 1ull << (dev & 63);
+    cudaError_t e = cudaSuccess;
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(k_batch<L, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geometry<L>::kBytes);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    if (ctas_per_sm)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_batch<L, VEC>, kThreads, Geometry<L>::kBytes);
+    return e;
+}
+
+template <class L, bool VEC>
+cudaError_t batch_launch(const BatchArgs& A, int grid, cudaStream_t s) {
+    k_batch<L, VEC><<<grid, kThreads, Geometry<L>::kBytes, s>>>(A);
+    return cudaGetLastError();
+}
+
 __global__ void k_diag_reduce(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
     __shared__ double red[kThreads / 32][kDiagSlots];
     double v[kDiagSlots] = {0, 0, 0, 0, 0, 0};
@@ -842,6 +925,31 @@ cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int 
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s) {
     k_diag_reduce<<<1, kThreads, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_batch(int precision, bool vec, int* ctas_per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    switch (precision) {
+        case kPrecF16:
+            return vec ? batch_configure<LayoutF16, true>(dev, ctas_per_sm)
+                       : batch_configure<LayoutF16, false>(dev, ctas_per_sm);
+        case kPrecB16:
+            return vec ? batch_configure<LayoutB16, true>(dev, ctas_per_sm)
+                       : batch_configure<LayoutB16, false>(dev, ctas_per_sm);
+        default:
+            return vec ? batch_configure<LayoutF32, true>(dev, ctas_per_sm)
+                       : batch_configure<LayoutF32, false>(dev, ctas_per_sm);
+    }
+}
+
+cudaError_t launch_batch(const BatchArgs& A, int precision, bool vec, int grid, cudaStream_t s) {
+    switch (precision) {
+        case kPrecF16: return vec ? batch_launch<LayoutF16, true>(A, grid, s) : batch_launch<LayoutF16, false>(A, grid, s);
+        case kPrecB16: return vec ? batch_launch<LayoutB16, true>(A, grid, s) : batch_launch<LayoutB16, false>(A, grid, s);
+        default: return vec ? batch_launch<LayoutF32, true>(A, grid, s) : batch_launch<LayoutF32, false>(A, grid, s);
+    }
 }
 
 }  // namespace cmrt

@@ -158,3 +158,24 @@ def buoyant_replica(side=512, seed=4, **kw):
     """Same generator on a side x side box with the drop count scaled by area."""
     ndrops = max(1, int(round(256 * side * side / (16384 * 8192))))
     return buoyant_drops(nx=side, ny=side, ndrops=ndrops, seed=seed, **kw)
+
+
+BATCH_SIDES = (64, 128, 256, 512)
+
+
+def batch_ensemble(n=512, seed=5, sides=BATCH_SIDES):
+    """``n`` independent periodic lattices: side drawn uniformly from ``sides``,
+    one centred drop of radius side/4, sigma uniform in [0.001, 0.02], Lambda
+    log-uniform in [1, 100] (heavy fluid inside).  Returns a list of
+    (params, rho^N_0 as float32, None) triples; u_0 = 0."""
+    rng = np.random.default_rng(seed)
+    side = rng.choice(np.asarray(sides), size=n)
+    sigma = rng.uniform(0.001, 0.02, size=n)
+    Lam = np.exp(rng.uniform(0.0, math.log(100.0), size=n))
+    members = []
+    for k in range(n):
+        s = int(side[k])
+        p = base_params(s, s, rho0_r=1.0, rho0_b=1.0 / float(Lam[k]), sigma=float(sigma[k]))
+        rho_n = drops_field(s, s, [(s / 2.0, s / 2.0)], [s / 4.0], dtype=np.float32)
+        members.append((p, rho_n, None))
+    return members

@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(cm):
 
 
 def test_abi_version_and_struct_size(cm):
-    assert cm.cmrt_abi_version() == 2
+    assert cm.cmrt_abi_version() == 4
     assert cm.load().cmrt_params_size() == ctypes.sizeof(cm.cmrt_params)
 
 
@@ -89,3 +89,33 @@ def test_make_params_from_workload_dict(cm):
     assert p.wall_y == 1 and abs(p.g_acc[0] - 1e-6) < 1e-18
     assert abs(p.alpha_r - 0.995) < 1e-12 and abs(p.rho0_b - 0.01) < 1e-15
     assert cm.cmrt_validate(p) == cm.CMRT_OK
+
+
+def test_batch_init_validates_before_touching_a_device(cm):
+    good = cm.make_params({"nx": 16, "ny": 16})
+    bad = cm.make_params({"nx": 16, "ny": 16})
+    bad.sigma = -1.0
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_batch_init([good, bad], None, None, 0)
+    assert ei.value.status == cm.CMRT_EINVAL and "member 1" in str(ei.value)
+    mixed = cm.make_params({"nx": 32, "ny": 8, "precision": 2})
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_batch_init([good, mixed], None, None, 0)
+    assert ei.value.status == cm.CMRT_EINVAL and "one storage precision" in str(ei.value)
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_batch_init([], None, None, 0)
+    assert ei.value.status == cm.CMRT_EINVAL
+
+
+def test_null_batch_calls(cm):
+    lib = cm.load()
+    assert lib.cmrt_batch_step(None, 1) == cm.CMRT_ESTATE
+    assert lib.cmrt_batch_tune(None, None, 0, None) == cm.CMRT_ESTATE
+    assert lib.cmrt_batch_set_rows(None, 8, 8, 0, 8) == cm.CMRT_ESTATE
+    assert lib.cmrt_batch_get_rows(None, 8, 8, 0) == -1
+    assert lib.cmrt_batch_size(None) == -1
+    assert lib.cmrt_batch_time(None) == -1
+    assert lib.cmrt_batch_launch_count(None) == -1
+    assert lib.cmrt_batch_work_items(None) == -1
+    assert lib.cmrt_batch_device_bytes(None) == 0
+    lib.cmrt_batch_destroy(None)  # no-op

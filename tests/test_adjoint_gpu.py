@@ -1,0 +1,242 @@
+"""Discrete adjoint of the CUDA step (cmrt_step_vjp, cmrt_adjoint) against the
+FP64 oracle adjoint (oracle/cmrt_adjoint.py, itself pinned by finite
+differences of the forward oracle) and against central finite differences of
+the FP64 forward oracle.
+
+Tolerances: the CUDA adjoint runs in FP32 on an FP32 forward trajectory.  One
+reverse step, given the same FP32 state, is compared element by element at
+2e-5 of the largest adjoint entry and parameter gradients at 1e-4 relative
+(FP32 rounding of O(1) populations, amplified by the 1/rho and 1/|grad rho^N|
+factors of the recolour and normal adjoints).  Over tens to hundreds of steps
+the FP32 forward trajectory itself moves the final colour field by ~1e-6, so
+J is compared at 1e-4 relative, and the objective's target is chosen so that
+the residual rho^N - target (O(0.1) at the interface) is far above that
+drift; gradients are then held to 1e-4 relative, the bar the target
+statement sets against finite differences.
+"""
+import numpy as np
+import pytest
+
+from oracle import cmrt_adjoint as A
+from oracle import cmrt_oracle as O
+from paper_2005_04642_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2005_04642_gb300 import cmrt as cm  # noqa: E402
+
+cm.load()
+
+PN = cm.ADJOINT_PARAMS
+
+
+def _state32(d, seed):
+    """An FP32 off-equilibrium state with a drop: (R, B) as float32."""
+    p = O.Params(**d)
+    rng = np.random.default_rng(seed)
+    rn = I.drops_field(d["nx"], d["ny"], [(d["nx"] / 2 + 0.3, d["ny"] / 2 - 0.2)], [min(d["nx"], d["ny"]) / 3.5],
+                       periodic_y=not d["wall_y"])
+    u = rng.uniform(-0.02, 0.02, size=(2, d["ny"], d["nx"]))
+    R, B = O.init_state(rn, u[0], u[1], p)
+    R, B = O.step(R, B, p)
+    R = R * (1.0 + 0.005 * rng.standard_normal(R.shape))
+    B = B * (1.0 + 0.005 * rng.standard_normal(B.shape))
+    return R.astype(np.float32), B.astype(np.float32)
+
+
+VJP_CASES = [
+    ("periodic", dict()),
+    ("walls_gravity", dict(wall_y=True, g_acc=(2e-4, -3e-4))),
+    ("rates_ghostN", dict(lambda3_r=1.5, lambda3_b=0.7, lambda6=1.2, lambda7=0.8, ghost_N_mode=1)),
+    ("visc_eta_fixedK", dict(visc_mode=1, eta=0.2, curvature_mode=1, fixed_K=0.05, g_vol=(1e-4, 0.0))),
+    ("ragged_walls", dict(wall_y=True, sigma=0.02)),
+]
+
+
+@pytest.mark.parametrize("name,kw", VJP_CASES)
+def test_step_vjp_matches_oracle_adjoint(name, kw):
+    nx, ny = (131, 37) if name == "ragged_walls" else (40, 24)
+    d = I.base_params(nx, ny, sigma=kw.pop("sigma", 0.01), **kw)
+    p = O.Params(**d)
+    R, B = _state32(d, seed=3)
+    lat = cm.Lattice(d, None, None)
+    lat.set_populations(np.stack([R, B]))
+    rng = np.random.default_rng(4)
+    lam_next = rng.standard_normal((2, 9, ny, nx)).astype(np.float32)
+    got, g = lat.step_vjp(lam_next)
+    lR, lB, gref = A.step_vjp(R.astype(np.float64), B.astype(np.float64), lam_next[0].astype(np.float64),
+                              lam_next[1].astype(np.float64), p)
+    ref = np.stack([lR, lB])
+    err = np.abs(got.double().cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err <= 2e-5, err
+    scale = max(abs(v) for v in gref.values())
+    for k, name_ in enumerate(PN):
+        assert abs(g[k] - gref[name_]) <= 1e-4 * max(abs(gref[name_]), 1e-3 * scale), (name_, g[k], gref[name_])
+    assert lat.time == 0  # the VJP does not advance the state
+    lat.close()
+
+
+def _drop_setup(n, radius, nsteps, g=1e-5, sigma=0.005, Lam=10.0, seed=9, wall=False, shift=(1.0, 0.5)):
+    d = I.base_params(n, n, rho0_r=1.0, rho0_b=1.0 / Lam, sigma=sigma, g_acc=(0.0, -g), wall_y=wall,
+                      lambda3_r=1.1, lambda3_b=0.9)
+    rn0 = I.drops_field(n, n, [(n / 2.0, n / 2.0)], [radius], periodic_y=not wall)
+    u0 = np.zeros((2, n, n))
+    # target: the final colour field of a run with sigma 5 % larger (Sec. 2
+    # force) from a drop displaced by `shift`, so that the residual at the
+    # interface is O(0.1), far above the FP32 drift of the forward run
+    pt = O.Params(**dict(d, sigma=1.05 * sigma))
+    rt0 = I.drops_field(n, n, [(n / 2.0 + shift[0], n / 2.0 + shift[1])], [radius], periodic_y=not wall)
+    Rt, Bt = O.run(*O.init_state(rt0, u0[0], u0[1], pt), pt, nsteps)
+    target = O.colour_index(Rt.sum(0), Bt.sum(0), pt)
+    return d, rn0, u0, target
+
+
+def _gpu_trajectory(d, rn32, u32, nsteps):
+    """Pre-collision FP32 states f(0..nsteps) of the CUDA forward run, as float64."""
+    lat = cm.Lattice(d, rn32, u32)
+    states = []
+    for t in range(nsteps + 1):
+        if t:
+            lat.step(1)
+        s = lat.populations().double().cpu().numpy()
+        states.append((s[0], s[1]))
+    lat.close()
+    return states
+
+
+@pytest.mark.parametrize("wall", [False, True])
+def test_adjoint_gradient_matches_oracle(wall):
+    """Through 30 steps with checkpoints every 7.  (a) The oracle adjoint
+    evaluated on the CUDA forward trajectory (the same FP32 states) isolates
+    the reverse arithmetic: FP32 rounding accumulated over 30 reverse steps,
+    held to 1e-4 of each gradient plus 1e-5 of the largest one (a component
+    that is a small sum of large, cancelling node contributions, here
+    dJ/dlambda3_b, is only known to that absolute level).  (b) The oracle's
+    own FP64 trajectory differs from the FP32 one by the drift of the forward
+    run, which moves the gradients by up to ~1e-3 here (gravity 1e-4 on a
+    radius-6 drop): that comparison is held to 3e-3 plus 1e-4 of the largest."""
+    nsteps, K = 30, 7
+    d, rn0, u0, target = _drop_setup(24, 6.0, nsteps, g=1e-4, wall=wall)
+    p = O.Params(**d)
+    rn32 = rn0.astype(np.float32)
+    u32 = u0.astype(np.float32)
+    lat = cm.Lattice(d, rn32, u32)
+    J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=K, want_rho_n0=True)
+    assert lat.time == nsteps
+    lat.close()
+    grn = grn.double().cpu().numpy()
+    # (a) same trajectory
+    states = _gpu_trajectory(d, rn32, u32, nsteps)
+    Ja = A.objective(*states[-1], target, p)
+    lR, lB = A.objective_vjp(*states[-1], target, p)
+    ga = {k: 0.0 for k in A.PARAM_NAMES}
+    for t in range(nsteps - 1, -1, -1):
+        lR, lB, gs = A.step_vjp(*states[t], lR, lB, p)
+        for k in ga:
+            ga[k] += gs[k]
+    grn_a = A.init_vjp(rn32.astype(np.float64), u0[0], u0[1], lR, lB, p)
+    assert abs(J - Ja) <= 1e-6 * Ja
+    gmax = max(abs(v) for v in ga.values())
+    for name_ in PN:
+        assert abs(g[name_] - ga[name_]) <= 1e-4 * abs(ga[name_]) + 1e-5 * gmax, (name_, g[name_], ga[name_])
+    assert np.abs(grn - grn_a).max() <= 1e-4 * np.abs(grn_a).max()
+    # (b) the FP64 trajectory
+    J_ref, g_ref, grn_ref = A.gradient_of_objective(rn32.astype(np.float64), u0[0], u0[1], target, p, nsteps, K)
+    assert abs(J - J_ref) <= 1e-4 * J_ref
+    for name_ in PN:
+        assert abs(g[name_] - g_ref[name_]) <= 3e-3 * abs(g_ref[name_]) + 1e-4 * gmax, (name_, g[name_], g_ref[name_])
+    assert np.abs(grn - grn_ref).max() <= 3e-3 * np.abs(grn_ref).max()
+
+
+def test_checkpoint_interval_gives_identical_gradients():
+    nsteps = 12
+    d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4)
+    outs = []
+    for K in (1, 5, 12, 200):
+        lat = cm.Lattice(d, rn0.astype(np.float32), None)
+        J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=K, want_rho_n0=True)
+        outs.append((J, g, grn.cpu().numpy()))
+        lat.close()
+    for J, g, grn in outs[1:]:
+        assert J == outs[0][0]
+        assert g == outs[0][1]
+        assert np.array_equal(grn, outs[0][2])
+
+
+def test_adjoint_matches_finite_differences_64():
+    """64^2 drop (radius 8), Lambda = 10, gravity 1e-5, 200 steps, checkpoints
+    every 50: gradients with respect to sigma, beta, both shear rates, the
+    body force and (one direction of) the initial colour field against
+    fourth-order central differences of the FP64 forward oracle (steps
+    chosen so that truncation and round-off stay below 1e-6 relative)."""
+    nsteps, K = 200, 50
+    d, rn0, u0, target = _drop_setup(64, 8.0, nsteps, g=1e-5)
+    p = O.Params(**d)
+    rn32 = rn0.astype(np.float32)
+    lat = cm.Lattice(d, rn32, None)
+    J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=K, want_rho_n0=True)
+    lat.close()
+
+    def J_of(q, rn):
+        R, B = O.run(*O.init_state(rn, u0[0], u0[1], q), q, nsteps)
+        return A.objective(R, B, target, q)
+
+    import dataclasses
+    h = {"sigma": 1e-5, "beta": 1e-4, "lambda3_r": 1e-4, "lambda3_b": 1e-4, "g_acc_x": 1e-6, "g_acc_y": 1e-6}
+
+    def shifted(name, s):
+        if name.startswith("g_acc"):
+            gg = list(p.g_acc)
+            gg[0 if name.endswith("x") else 1] += s
+            return dataclasses.replace(p, g_acc=tuple(gg))
+        return dataclasses.replace(p, **{name: getattr(p, name) + s})
+
+    rn64 = rn32.astype(np.float64)
+    for name_ in PN:
+        H = h[name_]
+        fd = (8 * (J_of(shifted(name_, H), rn64) - J_of(shifted(name_, -H), rn64))
+              - (J_of(shifted(name_, 2 * H), rn64) - J_of(shifted(name_, -2 * H), rn64))) / (12 * H)
+        assert abs(g[name_] - fd) <= 1e-4 * abs(fd), (name_, g[name_], fd)
+    v = np.random.default_rng(2).standard_normal(rn0.shape) * (np.abs(rn64) < 0.99)
+    H = 1e-5
+    fd = (8 * (J_of(p, rn64 + H * v) - J_of(p, rn64 - H * v))
+          - (J_of(p, rn64 + 2 * H * v) - J_of(p, rn64 - 2 * H * v))) / (12 * H)
+    ad = float(np.sum(grn.double().cpu().numpy() * v))
+    assert abs(ad - fd) <= 1e-4 * abs(fd), (ad, fd)
+
+
+def test_autograd_function():
+    nsteps = 20
+    d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4)
+    theta = torch.tensor([d["sigma"], d["beta"], d["lambda3_r"], d["lambda3_b"], 0.0, -1e-4],
+                         dtype=torch.float64, requires_grad=True)
+    rn = torch.from_numpy(rn0.astype(np.float32)).cuda().requires_grad_(True)
+    J = cm.colour_mismatch(theta, rn, d, torch.from_numpy(target.astype(np.float32)).cuda(), nsteps, 8)
+    J.backward()
+    lat = cm.Lattice(d, rn0.astype(np.float32), None)
+    J2, g2, grn2 = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=8, want_rho_n0=True)
+    lat.close()
+    assert float(J) == J2
+    assert theta.grad.tolist() == [g2[k] for k in PN]
+    assert torch.equal(rn.grad, grn2)
+
+
+def test_adjoint_rejects_bad_use():
+    d, _, _ = I.static_drop(n=16, radius=4.0)
+    lat = cm.Lattice(dict(d, precision=2), None, None)
+    with pytest.raises(cm.CmrtError) as ei:
+        lat.adjoint(2, np.zeros((16, 16), np.float32))
+    assert ei.value.status == cm.CMRT_EINVAL
+    lat.close()
+    lat = cm.Lattice(d, None, None)
+    lat.step(1)
+    with pytest.raises(cm.CmrtError) as ei:
+        lat.adjoint(2, np.zeros((16, 16), np.float32), want_rho_n0=True)
+    assert ei.value.status == cm.CMRT_EINVAL
+    J, g, _ = lat.adjoint(2, np.zeros((16, 16), np.float32))  # without rho^N_0 any time is fine
+    assert lat.time == 3 and J > 0
+    lat.close()
