@@ -21,7 +21,7 @@
 // with 16-byte cp.async copies, two rows ahead of use.  Each iteration runs
 // a wavefront of four stages on consecutive rows, each stage reading only
 // what the previous one left in shared memory:
-//   A (row s-1)  gather f, colour moments and fractions, Phi'   (tile + 3)
+//   A (row s-1)  gather f, colour moments, red fraction, Phi'  (tile + 3)
 //   B (row s-2)  grad rho^N and n-hat with the compact stencil   (tile + 2)
 //   C (row s-3)  K = div n-hat, force G, force-adjusted u        (tile + 1)
 //   D (row s-4)  grad Phi', div u, C_ab, MRT collision in moment
@@ -113,7 +113,7 @@ __device__ __forceinline__ void segregation(float sx, float sy, float (&seg)[9])
 // 32-bit: 18 FP32 planes.
 struct LayoutF32 {
     static constexpr int kSlotBytes = kPlanes * kWin * 4;
-    static constexpr bool kSplitA = false;  // ring A keeps the colour fractions for stage D
+    static constexpr bool kSplitA = false;  // ring A keeps the red fraction for stage D
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
     static constexpr size_t node_bytes() { return kPlanes * 4; }
@@ -326,10 +326,10 @@ using LayoutB16 = Layout16<__nv_bfloat162>;
 template <class L>
 struct Geometry {
     static constexpr int kPopBytes = kRing * L::kSlotBytes;
-    // ring A: without kSplitA, chi_R, chi_B, Phi', rho, j_x, j_y over 8 rows;
-    // with it, Phi' over 8 rows (ring Q) and chi_R, chi_B, rho, j_x, j_y over 4 rows
+    // ring A: without kSplitA, chi_R, Phi', rho, j_x, j_y over 8 rows; with it,
+    // Phi' over 8 rows (ring Q) and chi_R, rho, j_x, j_y over 4 rows
     static constexpr int kQFloats = L::kSplitA ? 8 * kWin : 0;
-    static constexpr int kAFloats = L::kSplitA ? 4 * 5 * kWin : 8 * 6 * kWin;
+    static constexpr int kAFloats = L::kSplitA ? 4 * 4 * kWin : 8 * 5 * kWin;
     static constexpr int kBytes = kPopBytes + 4 * (kQFloats + kAFloats + kBFloats + kCFloats);
 };
 
@@ -341,25 +341,22 @@ struct Rings {
     float* b;
     float* c;
     __device__ __forceinline__ const char* slot(int row) const { return pop + (row & (kRing - 1)) * L::kSlotBytes; }
-    // ring A fields: the colour fractions chi_R = a / (a + b), chi_B = b / (a + b)
-    // (a = rho_R / rho0_r, b = rho_B / rho0_b; rho^N = chi_R - chi_B, Eq. equ_rhoN_def)
+    // ring A fields: the red fraction chi_R = a / (a + b) (a = rho_R / rho0_r,
+    // b = rho_B / rho0_b; rho^N = 2 chi_R - 1, Eq. equ_rhoN_def)
     __device__ __forceinline__ float* chiR(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 5 + 0) * kWin : a + ((row & 7) * 6 + 0) * kWin;
-    }
-    __device__ __forceinline__ float* chiB(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 5 + 4) * kWin : a + ((row & 7) * 6 + 5) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 4 + 0) * kWin : a + ((row & 7) * 5 + 0) * kWin;
     }
     __device__ __forceinline__ float* phip(int row) const {
-        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 6 + 1) * kWin;
+        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 5 + 1) * kWin;
     }
     __device__ __forceinline__ float* rho(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 5 + 1) * kWin : a + ((row & 7) * 6 + 2) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 4 + 1) * kWin : a + ((row & 7) * 5 + 2) * kWin;
     }
     __device__ __forceinline__ float* jx(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 5 + 2) * kWin : a + ((row & 7) * 6 + 3) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 4 + 2) * kWin : a + ((row & 7) * 5 + 3) * kWin;
     }
     __device__ __forceinline__ float* jy(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 5 + 3) * kWin : a + ((row & 7) * 6 + 4) * kWin;
+        return L::kSplitA ? a + ((row & 3) * 4 + 3) * kWin : a + ((row & 7) * 5 + 4) * kWin;
     }
     __device__ __forceinline__ float* B(int row, int f) const { return b + (((row & 3) * kBF) + f) * kWin; }
     __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
@@ -460,26 +457,23 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
                                  (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
                 const float a = rr * P.inv_rho0_r;
                 const float b = rb * P.inv_rho0_b;
-                // colour fractions: rho^N = chi_R - chi_B (Eq. equ_rhoN_def); kept
-                // apart so that the smaller one carries the gradient of a nearly
-                // pure region without the FP32 cancellation of rho^N near +-1
+                // red fraction: rho^N = 2 chi_R - 1 (Eq. equ_rhoN_def); near pure
+                // blue chi_R is small and keeps the digits that rho^N, stored in
+                // FP32 next to -1, would lose
                 const float inv_ab = rcp(a + b);
-                const float chr = a * inv_ab, chb = b * inv_ab;
+                const float chr = a * inv_ab;
                 const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
                 R.chiR(ya)[t] = chr;
-                R.chiB(ya)[t] = chb;
                 R.phip(ya)[t] = phip;
                 R.rho(ya)[t] = rr + rb;
                 R.jx(ya)[t] = jx;
                 R.jy(ya)[t] = jy;
                 if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
                     R.chiR(-1)[t] = chr;
-                    R.chiB(-1)[t] = chb;
                     R.phip(-1)[t] = phip;
                 }
                 if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
                     R.chiR(ny)[t] = chr;
-                    R.chiB(ny)[t] = chb;
                     R.phip(ny)[t] = phip;
                 }
             }
@@ -490,11 +484,9 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
         {
             const int yb = s - 2;
             if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-                // grad rho^N = 2 grad chi_R = -2 grad chi_B (the stencil weights sum
-                // to zero), taken on the fraction that is the smaller at this node
-                const bool red_minor = R.chiR(yb)[t] < R.chiB(yb)[t];
-                auto ch_row = [&](int r) { return red_minor ? R.chiR(r) : R.chiB(r); };
-                const float sgn = red_minor ? 2.0f : -2.0f;
+                // grad rho^N = 2 grad chi_R (the stencil weights sum to zero)
+                auto ch_row = [&](int r) { return R.chiR(r); };
+                const float sgn = 2.0f;
                 const float gx = sgn * ddx_at(ch_row, yb, t);
                 const float gy = sgn * ddy_at(ch_row, yb, t);
                 // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
