@@ -83,7 +83,11 @@ typedef struct {
     int32_t visc_mode;       /* 0: nu linear in rho^N between the pure fluids;
                                 1: constant shear viscosity eta, nu = eta / rho                  */
     double eta;              /* shear viscosity for visc_mode 1                                   */
-    int32_t stencil_order;   /* 2: compact isotropic gradients (Sec. 2) -- the only order built   */
+    int32_t stencil_order;   /* 2: compact isotropic gradients (Sec. 2), fused one-kernel step;
+                                6: App. B's order-6 stencil for grad rho^N and grad Phi' (radius 3;
+                                K and div u stay compact), run as four plane passes; FP32 storage
+                                only, ny >= 3 with walls, not in batches or
+                                cmrt_diagnostics_noalloc                                         */
     int32_t curvature_mode;  /* 0: K = div n-hat; 1: K = fixed_K (Sec. 4.2)                        */
     double fixed_K;
     int32_t ghost_N_mode;    /* 0: N relaxes to h^(6).f^(0) (App. A); 1: N relaxes to 0 (Table 1) */

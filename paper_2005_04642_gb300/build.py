@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcmrt.so")
 
-SOURCES = ["cmrt_api.cu", "cmrt_step.cu", "cmrt_aux.cu", "cmrt_adjoint.cu"]
+SOURCES = ["cmrt_api.cu", "cmrt_step.cu", "cmrt_aux.cu", "cmrt_planes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
           "-Xcompiler", "-O3", "-I", INCLUDE, "-I", CSRC]

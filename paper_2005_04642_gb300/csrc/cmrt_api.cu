@@ -164,9 +164,12 @@ cmrt_status validate(const cmrt_params* p) {
     if (p->visc_mode != 0 && p->visc_mode != 1) return fail(nullptr, CMRT_EINVAL, "visc_mode must be 0 or 1");
     if (p->visc_mode == 1 && !(p->eta > 0 && finite(p->eta)))
         return fail(nullptr, CMRT_EINVAL, "eta must be finite and > 0 for visc_mode 1");
-    if (p->stencil_order != 2)
-        return fail(nullptr, CMRT_EINVAL, "stencil_order %d is not built (only the compact order 2 is)",
-                    p->stencil_order);
+    if (p->stencil_order != 2 && p->stencil_order != 6)
+        return fail(nullptr, CMRT_EINVAL, "stencil_order must be 2 (compact) or 6 (App. B), got %d", p->stencil_order);
+    if (p->stencil_order == 6 && p->precision != 0)
+        return fail(nullptr, CMRT_EINVAL, "stencil_order 6 needs FP32 storage (precision 0)");
+    if (p->stencil_order == 6 && p->wall_y && p->ny < 3)
+        return fail(nullptr, CMRT_EINVAL, "stencil_order 6 with walls needs ny >= 3 (mirror rows of the radius-3 stencil)");
     if (p->curvature_mode != 0 && p->curvature_mode != 1)
         return fail(nullptr, CMRT_EINVAL, "curvature_mode must be 0 or 1");
     if (!finite(p->fixed_K)) return fail(nullptr, CMRT_EINVAL, "fixed_K must be finite");
@@ -188,6 +191,7 @@ StepParams derive(const cmrt_params& p) {
     s.visc_mode = p.visc_mode;
     s.curvature_mode = p.curvature_mode;
     s.ghost_N_mode = p.ghost_N_mode;
+    s.stencil_order = p.stencil_order;
     const double Lam = p.rho0_r / p.rho0_b;
     s.inv_rho0_r = static_cast<float>(1.0 / p.rho0_r);
     s.inv_rho0_b = static_cast<float>(1.0 / p.rho0_b);
@@ -324,6 +328,26 @@ cmrt_status check_flag(Ctx* c) {
     return CMRT_OK;
 }
 
+// One step src -> dst: the fused kernel, or the plane passes for the order-6
+// stencil.  Returns the number of kernels launched, or -1 on a launch error.
+int step_once(Ctx* c, const void* src, void* dst, cudaError_t* err) {
+    if (c->p.stencil_order == 6) {
+        *err = cmrt::launch_step_planes(static_cast<const float*>(src), static_cast<float*>(dst), c->sp,
+                                        c->adj_scratch, c->d_flag, c->stream);
+        return *err == cudaSuccess ? 4 : -1;
+    }
+    *err = cmrt::launch_step(src, dst, c->sp, c->rows, c->d_flag, c->stream);
+    return *err == cudaSuccess ? 1 : -1;
+}
+
+#define STEP(ctx, src, dst)                                                                          \
+    do {                                                                                             \
+        cudaError_t e_ = cudaSuccess;                                                                \
+        const int k_ = step_once((ctx), (src), (dst), &e_);                                          \
+        if (k_ < 0) return fail((ctx), CMRT_ECUDA, "step launch failed: %s", cudaGetErrorString(e_)); \
+        (ctx)->launches += k_;                                                                       \
+    } while (0)
+
 // Writes the state at t = 0 into c->buf[c->cur] (Eqs. equ_rhoN_def, equ_equ):
 // the equilibrium of the colour field rho_n0 and velocity u0 (host or device
 // pointers, NULL for -1 and 0).
@@ -445,6 +469,19 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
     c->rows = cmrt::chain_rows(p->nx, p->ny, sms, p->precision);
     const dim3 g = cmrt::chain_grid(p->nx, p->ny, c->rows);
     c->n_partials = static_cast<int>(g.x * g.y);
+    if (p->stencil_order == 6) {
+        // the order-6 passes keep their fields in the scratch planes and write
+        // one partial row per 128-column block of a lattice row
+        c->n_partials = std::max(c->n_partials, cmrt::adj_blocks(p->nx, p->ny));
+        const size_t bytes = cmrt::kAdjPlanes * cells(*c) * sizeof(float);
+        if (cudaMalloc(&c->adj_scratch, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->adj_scratch = nullptr;
+            fail(c, CMRT_ENOMEM, "cudaMalloc of %zu scratch bytes for the order-6 step failed", bytes);
+            return bail(CMRT_ENOMEM);
+        }
+        c->adj_bytes += bytes;
+    }
     if (cudaMalloc(&c->d_flag, sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&c->d_partials, sizeof(double) * cmrt::kDiagSlots * c->n_partials) != cudaSuccess ||
         cudaMalloc(&c->d_diag, sizeof(double) * cmrt::kDiagSlots) != cudaSuccess) {
@@ -473,8 +510,7 @@ cmrt_status cmrt_step(cmrt_ctx* h, int64_t n) {
     if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
     for (int64_t k = 0; k < n; ++k) {
-        CK(c, cmrt::launch_step(c->buf[c->cur], c->buf[c->cur ^ 1], c->sp, c->rows, c->d_flag, c->stream));
-        c->launches++;
+        STEP(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
         c->cur ^= 1;
         c->t++;
         if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
@@ -499,9 +535,15 @@ cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, floa
         if (!outs[k]) dev[k] = nullptr;
         else dev[k] = is_device_ptr(outs[k]) ? outs[k] : c->stg->ptr + k * n;
     }
-    CK(c, cmrt::launch_fields(c->buf[c->cur], c->sp, c->rows, cmrt::FieldOut{dev[0], dev[1], dev[2], dev[3], dev[4]},
-                              c->stream));
-    c->launches++;
+    const cmrt::FieldOut fo{dev[0], dev[1], dev[2], dev[3], dev[4]};
+    if (c->p.stencil_order == 6) {
+        CK(c, cmrt::launch_fields_planes(static_cast<const float*>(c->buf[c->cur]), c->sp, c->adj_scratch, fo,
+                                         c->stream));
+        c->launches += 4;
+    } else {
+        CK(c, cmrt::launch_fields(c->buf[c->cur], c->sp, c->rows, fo, c->stream));
+        c->launches++;
+    }
     if (any_host) {
         for (int k = 0; k < 5; ++k)
             if (outs[k] && dev[k] != outs[k])
@@ -516,9 +558,16 @@ cmrt_status cmrt_diagnostics(cmrt_ctx* h, double out[6]) {
     if (!c) return CMRT_ESTATE;
     if (!out) return fail(c, CMRT_EINVAL, "out is NULL");
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
-    CK(c, cmrt::launch_diag_partials(c->buf[c->cur], c->sp, c->rows, c->d_partials, c->stream));
-    CK(c, cmrt::launch_diag_reduce(c->d_partials, c->n_partials, c->d_diag, c->stream));
-    c->launches += 2;
+    if (c->p.stencil_order == 6) {
+        CK(c, cmrt::launch_diag_planes(static_cast<const float*>(c->buf[c->cur]), c->sp, c->adj_scratch,
+                                       c->d_partials, c->stream));
+        CK(c, cmrt::launch_diag_reduce(c->d_partials, cmrt::adj_blocks(c->p.nx, c->p.ny), c->d_diag, c->stream));
+        c->launches += 5;
+    } else {
+        CK(c, cmrt::launch_diag_partials(c->buf[c->cur], c->sp, c->rows, c->d_partials, c->stream));
+        CK(c, cmrt::launch_diag_reduce(c->d_partials, c->n_partials, c->d_diag, c->stream));
+        c->launches += 2;
+    }
     double h6[cmrt::kDiagSlots];
     CK(c, cudaMemcpyAsync(h6, c->d_diag, sizeof h6, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -656,6 +705,8 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
     cmrt_status st = validate(p);
     if (st != CMRT_OK) return st;
     if (!pops || !out) return fail(nullptr, CMRT_EINVAL, "pops and out must not be NULL");
+    if (p->stencil_order != 2)
+        return fail(nullptr, CMRT_EINVAL, "stencil_order 6 needs a context (its passes keep fields in scratch planes)");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
@@ -979,6 +1030,8 @@ cmrt_status cmrt_batch_init(int32_t n, const cmrt_params* params, const float* c
         if (st != CMRT_OK) return bfail(nullptr, st, "member %d: %s", m, g_thread_error.c_str());
         if (params[m].precision != params[0].precision)
             return bfail(nullptr, CMRT_EINVAL, "member %d: all members must share one storage precision", m);
+        if (params[m].stencil_order != 2)
+            return bfail(nullptr, CMRT_EINVAL, "member %d: batches run the fused compact-stencil step only", m);
     }
     cmrt_batch* h = new (std::nothrow) cmrt_batch;
     if (!h) return bfail(nullptr, CMRT_ENOMEM, "host allocation of the batch failed");
@@ -1345,15 +1398,15 @@ cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
         return CMRT_OK;
     };
     cmrt_status st = CMRT_OK;
-    if (!c->adj_scratch) {
-        const size_t nb = static_cast<size_t>(cmrt::adj_blocks(c->p.nx, c->p.ny));
-        if ((st = grow(reinterpret_cast<void**>(&c->adj_scratch), cmrt::kAdjPlanes * n * sizeof(float))) ||
-            (st = grow(reinterpret_cast<void**>(&c->adj_partials), nb * cmrt::kAdjSlots * sizeof(double))) ||
-            (st = grow(reinterpret_cast<void**>(&c->adj_out), cmrt::kAdjSlots * sizeof(double))) ||
-            (st = grow(reinterpret_cast<void**>(&c->adj_lam[0]), state)) ||
-            (st = grow(reinterpret_cast<void**>(&c->adj_lam[1]), state)))
-            return st;
-    }
+    const size_t nb = static_cast<size_t>(cmrt::adj_blocks(c->p.nx, c->p.ny));
+    if (!c->adj_scratch && (st = grow(reinterpret_cast<void**>(&c->adj_scratch), cmrt::kAdjPlanes * n * sizeof(float))))
+        return st;
+    if (!c->adj_partials &&
+        (st = grow(reinterpret_cast<void**>(&c->adj_partials), nb * cmrt::kAdjSlots * sizeof(double))))
+        return st;
+    if (!c->adj_out && (st = grow(reinterpret_cast<void**>(&c->adj_out), cmrt::kAdjSlots * sizeof(double)))) return st;
+    for (float*& l : c->adj_lam)
+        if (!l && (st = grow(reinterpret_cast<void**>(&l), state))) return st;
     if (ckpt > c->adj_ckpt_cap) {
         CK(c, cudaStreamSynchronize(c->stream));
         if (c->adj_ckpt) cudaFree(c->adj_ckpt), c->adj_ckpt = nullptr, c->adj_bytes -= c->adj_ckpt_cap * state;
@@ -1447,8 +1500,7 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
     CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
     for (int64_t t = 0; t < nsteps; ++t) {
-        CK(c, cmrt::launch_step(c->buf[c->cur], c->buf[c->cur ^ 1], c->sp, c->rows, c->d_flag, c->stream));
-        c->launches++;
+        STEP(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
         c->cur ^= 1;
         c->t++;
         if ((t + 1) % K == 0 && t + 1 < nsteps)
@@ -1466,9 +1518,7 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
         const float* ck = c->adj_ckpt + static_cast<size_t>(k) * n18;
         auto state_of = [&](int64_t j) { return j == 0 ? ck : c->adj_seg + static_cast<size_t>(j - 1) * n18; };
         for (int64_t j = 1; j < s1 - s0; ++j) {
-            CK(c, cmrt::launch_step(state_of(j - 1), c->adj_seg + static_cast<size_t>(j - 1) * n18, c->sp, c->rows,
-                                    c->d_flag, c->stream));
-            c->launches++;
+            STEP(c, state_of(j - 1), c->adj_seg + static_cast<size_t>(j - 1) * n18);
         }
         for (int64_t t = s1 - 1; t >= s0; --t) {
             CK(c, cmrt::launch_adjoint_step(state_of(t - s0), c->adj_lam[a], c->sp, c->adj_scratch, c->adj_partials,

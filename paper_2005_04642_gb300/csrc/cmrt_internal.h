@@ -20,6 +20,7 @@ struct StepParams {
     int precision;                 // kPrecF32 / kPrecB16 / kPrecF16
     float psi_r[3], psi_b[3];      // 16-bit storage reference weights (rest, axis, diagonal)
     int visc_mode, curvature_mode, ghost_N_mode;
+    int stencil_order;             // 2: compact gradients; 6: App. B for grad rho^N and grad Phi'
     float inv_rho0_r, inv_rho0_b;  // colour index (Eq. equ_rhoN_def)
     float alpha_r, alpha_b;        // rest weights phi_0 (Eq. eq_phi)
     float kphi_r, kphi_b;          // 9/5 (1 - alpha_C): phi_i = w_i (kphi_r rho_R + kphi_b rho_B) / rho
@@ -101,7 +102,18 @@ cudaError_t prepare_batch(int precision, bool vec, int* ctas_per_sm);
 // One step of every member of a batch: `grid` persistent CTAs drain the work list.
 cudaError_t launch_batch(const BatchArgs& A, int precision, bool vec, int grid, cudaStream_t s);
 
-// Discrete adjoint (cmrt_adjoint.cu), FP32 storage.  scratch: float[kAdjPlanes][ny][nx];
+// Plane passes (cmrt_planes.cu), FP32 storage: one thread per node, the
+// intermediate fields in scratch planes float[kAdjPlanes][ny][nx].
+// The step, fields and diagnostics with the order-6 gradient (App. B); each
+// launches 4 kernels, diagnostics write partials[adj_blocks][kDiagSlots].
+cudaError_t launch_step_planes(const float* post, float* dst, const StepParams& P, float* scratch, unsigned* flag,
+                               cudaStream_t s);
+cudaError_t launch_fields_planes(const float* post, const StepParams& P, float* scratch, FieldOut out,
+                                 cudaStream_t s);
+cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* scratch, double* partials,
+                               cudaStream_t s);
+
+// Discrete adjoint (cmrt_planes.cu), FP32 storage.  scratch: float[kAdjPlanes][ny][nx];
 // partials: double[adj_blocks][kAdjSlots], accumulated by every launch (zero it
 // before the first): slots 0..5 = dJ/d(sigma, beta, lambda3_r, lambda3_b,
 // g_acc_x, g_acc_y), slot 6 = J.

@@ -1,5 +1,15 @@
-// Discrete adjoint (reverse mode) of the fused chromodynamic MRT step
-// (arXiv 2005.04642, Sec. 2, App. A) for FP32 storage.
+// Per-node plane passes (one thread per node, intermediate fields in global
+// planes) for FP32 storage: the step with App. B's order-6 gradient stencil,
+// and the discrete adjoint (reverse mode) of the step, arXiv 2005.04642,
+// Sec. 2, App. A, App. B.
+//
+// Order-6 step.  App. B's non-compact stencil d_a X = sum_N a_N sum_i w_i
+// X(r + N c_i) c_ia, (a_1, a_2, a_3) = (9/2, -9/10, 1/10), has radius 3; used
+// for grad rho^N and grad Phi' it widens the step's dependency radius from 3
+// to 5.  Rather than a second fused kernel with a wider halo and deeper
+// rings, the order-6 step runs as four passes over planes: moments, grad
+// rho^N, K / G / u (k_fwd_*, shared with the adjoint), then k_step_planes
+// (grad Phi', div u, collision, recolour, store).
 //
 // The forward step maps the post-collision state P_{t-1} to P_t:
 //   f(t) = gather(P_{t-1})                       (streaming, Eq. equ_evolution)
@@ -64,36 +74,63 @@ struct Lat {
         if (y >= ny) return parity * a[at(x, 2 * ny - 1 - y)];
         return a[at(x, y)];
     }
-    // compact gradient (Sec. 2) of a plane at (x, y)
+    // gradient of a plane at (x, y): the compact stencil (Sec. 2) for ORDER 2,
+    // App. B's radius-3 stencil for ORDER 6
+    template <int ORDER>
     __device__ __forceinline__ void grad(const float* a, int x, int y, float parity, float& gx, float& gy) const {
-        const float e = val(a, x + 1, y, parity), w = val(a, x - 1, y, parity);
-        const float n_ = val(a, x, y + 1, parity), s = val(a, x, y - 1, parity);
-        const float ne = val(a, x + 1, y + 1, parity), nw = val(a, x - 1, y + 1, parity);
-        const float se = val(a, x + 1, y - 1, parity), sw = val(a, x - 1, y - 1, parity);
-        gx = ddx(e, w, ne, nw, se, sw);
-        gy = ddy(n_, s, ne, nw, se, sw);
+        if (ORDER == 2) {
+            const float e = val(a, x + 1, y, parity), w = val(a, x - 1, y, parity);
+            const float n_ = val(a, x, y + 1, parity), s = val(a, x, y - 1, parity);
+            const float ne = val(a, x + 1, y + 1, parity), nw = val(a, x - 1, y + 1, parity);
+            const float se = val(a, x + 1, y - 1, parity), sw = val(a, x - 1, y - 1, parity);
+            gx = ddx(e, w, ne, nw, se, sw);
+            gy = ddy(n_, s, ne, nw, se, sw);
+        } else {
+            gx = 0.0f;
+            gy = 0.0f;
+#pragma unroll
+            for (int N = 1; N <= 3; ++N) {
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const float v = val(a, x + N * lcx(i), y + N * lcy(i), parity);
+                    if (lcx(i)) gx = fmaf(order6_coef(N) * lw(i) * float(lcx(i)), v, gx);
+                    if (lcy(i)) gy = fmaf(order6_coef(N) * lw(i) * float(lcy(i)), v, gy);
+                }
+            }
+        }
     }
-    // transpose of one component (XC: x, else y) of the compact gradient,
-    // applied to a plane: sum_i 3 w_i c_i a(r - c_i) over nodes r - c_i of
-    // the lattice, plus, in a wall row, the row's own nodes whose stencil
-    // read this node as a mirrored ghost
-    template <bool XC>
+    // transpose of one component (XC: x, else y) of grad<ORDER>, applied to
+    // a plane: sum over the stencil's reach N c_i of k a(r - N c_i) for nodes
+    // of the lattice, plus, next to a wall, the nodes whose stencil read this
+    // node as a mirrored ghost (mirror row -1 - y' below, 2 ny - 1 - y' above)
+    template <bool XC, int ORDER>
     __device__ __forceinline__ float gradT(const float* a, int x, int y, float parity) const {
         float acc = 0.0f;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const int c = XC ? lcx(i) : lcy(i);
-            if (c == 0) continue;
-            const float k = 3.0f * lw(i) * float(c);
-            const int sy = y - lcy(i);
-            if (!walls || (sy >= 0 && sy < ny)) acc = fmaf(k, a[at(wx(x - lcx(i)), wy(sy))], acc);
-            if (walls) {
-                if (y == 0 && lcy(i) == -1) acc = fmaf(parity * k, a[at(wx(x - lcx(i)), 0)], acc);
-                if (y == ny - 1 && lcy(i) == 1) acc = fmaf(parity * k, a[at(wx(x - lcx(i)), ny - 1)], acc);
+        for (int N = 1; N <= (ORDER == 6 ? 3 : 1); ++N) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int c = XC ? lcx(i) : lcy(i);
+                if (c == 0) continue;
+                const float k = (ORDER == 6 ? order6_coef(N) : 3.0f) * lw(i) * float(c);
+                const int xs = wx(x - N * lcx(i));
+                const int dy = N * lcy(i);
+                const int ys = y - dy;
+                if (!walls) {
+                    acc = fmaf(k, a[at(xs, wy(ys))], acc);
+                } else {
+                    if (ys >= 0 && ys < ny) acc = fmaf(k, a[at(xs, ys)], acc);
+                    const int yb = -1 - y - dy;  // node whose read below y = -1/2 mirrors onto row y
+                    if (yb >= 0 && yb < ny && yb + dy < 0) acc = fmaf(parity * k, a[at(xs, yb)], acc);
+                    const int yt = 2 * ny - 1 - y - dy;  // same above y = ny - 1/2
+                    if (yt >= 0 && yt < ny && yt + dy >= ny) acc = fmaf(parity * k, a[at(xs, yt)], acc);
+                }
             }
         }
         return acc;
     }
+    // App. B coefficients a_N of the order-6 stencil
+    __host__ __device__ static constexpr float order6_coef(int N) { return N == 1 ? 4.5f : (N == 2 ? -0.9f : 0.1f); }
 };
 
 __device__ __forceinline__ Lat lattice(const StepParams& P) {
@@ -195,15 +232,14 @@ __global__ void __launch_bounds__(kAT) k_fwd_normal(const StepParams P, float* _
     // zero): the same stencil, evaluated on the fraction that is small here
     const size_t o = L.at(x, y);
     float gx, gy;
-    if (S[kCHR * L.n + o] < S[kCHB * L.n + o]) {
-        L.grad(S + kCHR * L.n, x, y, 1.0f, gx, gy);
-        gx *= 2.0f;
-        gy *= 2.0f;
-    } else {
-        L.grad(S + kCHB * L.n, x, y, 1.0f, gx, gy);
-        gx *= -2.0f;
-        gy *= -2.0f;
-    }
+    const bool red_minor = S[kCHR * L.n + o] < S[kCHB * L.n + o];
+    const float* ch = S + (red_minor ? kCHR : kCHB) * L.n;
+    if (P.stencil_order == 6)
+        L.grad<6>(ch, x, y, 1.0f, gx, gy);
+    else
+        L.grad<2>(ch, x, y, 1.0f, gx, gy);
+    gx *= red_minor ? 2.0f : -2.0f;
+    gy *= red_minor ? 2.0f : -2.0f;
     S[kGX * L.n + o] = gx;
     S[kGY * L.n + o] = gy;
 }
@@ -269,9 +305,12 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
         const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
         const float rn = S[kCHR * L.n + o] - S[kCHB * L.n + o];
         float dPx, dPy, dux, duy, t0, t1;
-        L.grad(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
-        L.grad(S + kUX * L.n, x, y, -1.0f, dux, t0);
-        L.grad(S + kUY * L.n, x, y, -1.0f, t1, duy);
+        if (P.stencil_order == 6)
+            L.grad<6>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
+        else
+            L.grad<2>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
+        L.grad<2>(S + kUX * L.n, x, y, -1.0f, dux, t0);
+        L.grad<2>(S + kUY * L.n, x, y, -1.0f, t1, duy);
         const float divu = dux + duy;
         // ---- forward values at this node
         float nu, dnu_drn = 0.0f;
@@ -448,8 +487,8 @@ __global__ void __launch_bounds__(kAT) k_rev_force(const StepParams P, float* __
     double acc[3] = {0.0, 0.0, 0.0};  // sigma, g_acc_x, g_acc_y
     if (x < L.nx) {
         const size_t o = L.at(x, y);
-        const float uxt = S[kUXB * L.n + o] + L.gradT<true>(S + kDIVUB * L.n, x, y, -1.0f);
-        const float uyt = S[kUYB * L.n + o] + L.gradT<false>(S + kDIVUB * L.n, x, y, -1.0f);
+        const float uxt = S[kUXB * L.n + o] + L.gradT<true, 2>(S + kDIVUB * L.n, x, y, -1.0f);
+        const float uyt = S[kUYB * L.n + o] + L.gradT<false, 2>(S + kDIVUB * L.n, x, y, -1.0f);
         const float rho = S[kRR * L.n + o] + S[kRB * L.n + o];
         const float ir = 1.0f / rho;
         const float ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
@@ -479,8 +518,8 @@ __global__ void __launch_bounds__(kAT) k_rev_normal(const StepParams P, float* _
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx) return;
     const size_t o = L.at(x, y);
-    const float nxb = L.gradT<true>(S + kKB * L.n, x, y, 1.0f);
-    const float nyb = L.gradT<false>(S + kKB * L.n, x, y, -1.0f);
+    const float nxb = L.gradT<true, 2>(S + kKB * L.n, x, y, 1.0f);
+    const float nyb = L.gradT<false, 2>(S + kKB * L.n, x, y, -1.0f);
     float tx, ty;
     normalise_T(S[kGX * L.n + o], S[kGY * L.n + o], nxb, nyb, tx, ty);
     S[kGXB * L.n + o] -= tx;
@@ -494,9 +533,14 @@ __global__ void __launch_bounds__(kAT) k_rev_moments(const StepParams P, float* 
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx) return;
     const size_t o = L.at(x, y);
-    const float rnb = S[kRNB * L.n + o] + L.gradT<true>(S + kGXB * L.n, x, y, 1.0f) +
-                      L.gradT<false>(S + kGYB * L.n, x, y, 1.0f);
-    const float phb = L.gradT<true>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false>(S + kDPYB * L.n, x, y, 1.0f);
+    float rnb = S[kRNB * L.n + o], phb;
+    if (P.stencil_order == 6) {
+        rnb += L.gradT<true, 6>(S + kGXB * L.n, x, y, 1.0f) + L.gradT<false, 6>(S + kGYB * L.n, x, y, 1.0f);
+        phb = L.gradT<true, 6>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false, 6>(S + kDPYB * L.n, x, y, 1.0f);
+    } else {
+        rnb += L.gradT<true, 2>(S + kGXB * L.n, x, y, 1.0f) + L.gradT<false, 2>(S + kGYB * L.n, x, y, 1.0f);
+        phb = L.gradT<true, 2>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false, 2>(S + kDPYB * L.n, x, y, 1.0f);
+    }
     const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
     const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
     const float iden = 1.0f / ((a + b) * (a + b));
@@ -620,6 +664,105 @@ __global__ void __launch_bounds__(kAT) k_init_T(const float* __restrict__ pre0, 
     grad[o] = 0.5f * (rrb / P.inv_rho0_r - rbb / P.inv_rho0_b);
 }
 
+// ----------------------------------------------------------------- order-6 step and its outputs
+// The rest of one step after k_fwd_*: grad Phi' (order of P.stencil_order),
+// div u, collision in moment space, recolour and store of P_t (FP32 layout).
+__global__ void __launch_bounds__(kAT) k_step_planes(const float* __restrict__ post, float* __restrict__ dst,
+                                                      const StepParams P, const float* __restrict__ S,
+                                                      unsigned* __restrict__ flag) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+    float fr[9], fb[9], f[9];
+    gather_node(post, L, x, y, fr, fb);
+    const float rr = sum9f(fr), rb = sum9f(fb);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
+    const float rho = rr + rb;
+    if (!isfinite(rho)) atomicOr(flag, 1u);
+    float dPx, dPy, dux, duy, t0, t1;
+    if (P.stencil_order == 6)
+        L.grad<6>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
+    else
+        L.grad<2>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
+    L.grad<2>(S + kUX * L.n, x, y, -1.0f, dux, t0);
+    L.grad<2>(S + kUY * L.n, x, y, -1.0f, t1, duy);
+    const float inv_rho = rcp(rho);
+    float nu;
+    if (P.visc_mode == 0) {
+        const float rn = S[kCHR * L.n + o] - S[kCHB * L.n + o];
+        nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
+    } else {
+        nu = P.eta * inv_rho;
+    }
+    float fp[9];
+    collide_increment(f, rr, rb, rho, nu, S[kUX * L.n + o], S[kUY * L.n + o], S[kGFX * L.n + o],
+                      S[kGFY * L.n + o], dPx, dPy, dux + duy, P, fp);
+    // recolour along e = grad rho^N / max(|grad rho^N|, eps) (Eq. eq_re_color)
+    const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
+    const float mag2 = fmaf(gx, gx, gy * gy);
+    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
+    const float sg = P.beta * (rr * rb) * inv_rho * phim * inv;
+    store_recoloured_f32(dst + o, L.n, fp, rr, rb, inv_rho, sg * gx, sg * gy);
+}
+
+__global__ void __launch_bounds__(kAT) k_fields_planes(const StepParams P, const float* __restrict__ S,
+                                                        FieldOut fo) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const size_t o = L.at(x, y);
+    const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
+    if (fo.rho_r) fo.rho_r[o] = rr;
+    if (fo.rho_b) fo.rho_b[o] = rb;
+    if (fo.ux) fo.ux[o] = S[kUX * L.n + o];
+    if (fo.uy) fo.uy[o] = S[kUY * L.n + o];
+    if (fo.p) fo.p[o] = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+}
+
+// FP64 per-CTA partial diagnostics, partials[block][kDiagSlots] (slot 4 is a maximum)
+__global__ void __launch_bounds__(kAT) k_diag_planes(const StepParams P, const float* __restrict__ S,
+                                                      double* __restrict__ partials) {
+    const Lat L = lattice(P);
+    const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
+    double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < L.nx) {
+        const size_t o = L.at(x, y);
+        const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
+        if (isfinite(rr + rb)) {
+            const double ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
+            v[0] = rr;
+            v[1] = rb;
+            v[2] = S[kJX * L.n + o];
+            v[3] = S[kJY * L.n + o];
+            v[4] = ux * ux + uy * uy;
+        } else {
+            v[5] = 1.0;
+        }
+    }
+    __shared__ double red[kAT / 32][kDiagSlots];
+#pragma unroll
+    for (int j = 0; j < kDiagSlots; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v[j], off);
+            v[j] = j == 4 ? fmax(v[j], w) : v[j] + w;
+        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < kDiagSlots; ++j) red[warp][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x < kDiagSlots) {
+        double acc = red[0][threadIdx.x];
+        for (int w = 1; w < kAT / 32; ++w)
+            acc = threadIdx.x == 4 ? fmax(acc, red[w][threadIdx.x]) : acc + red[w][threadIdx.x];
+        partials[(static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * kDiagSlots + threadIdx.x] = acc;
+    }
+}
+
 __global__ void k_adj_reduce(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
     __shared__ double red[kAT / 32][kAdjSlots];
     double v[kAdjSlots];
@@ -646,13 +789,19 @@ __global__ void k_adj_reduce(const double* __restrict__ partials, int nblocks, d
 
 dim3 adj_grid(const StepParams& P) { return dim3(static_cast<unsigned>((P.nx + kAT - 1) / kAT), P.ny, 1); }
 
-// the reverse passes shared by both forms of one adjoint step
-cudaError_t reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
-                         cudaStream_t s) {
+// moments, colour fractions, Phi', grad rho^N, K, G and u of P_{t-1} into the planes
+void forward_planes(const float* post, const StepParams& P, float* S, cudaStream_t s) {
     const dim3 g = adj_grid(P);
     k_fwd_moments<<<g, kAT, 0, s>>>(post, P, S);
     k_fwd_normal<<<g, kAT, 0, s>>>(P, S);
     k_fwd_force<<<g, kAT, 0, s>>>(P, S);
+}
+
+// the reverse passes shared by both forms of one adjoint step
+cudaError_t reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
+                         cudaStream_t s) {
+    const dim3 g = adj_grid(P);
+    forward_planes(post, P, S, s);
     k_rev_collide<<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
     k_rev_force<<<g, kAT, 0, s>>>(P, S, partials);
     if (P.curvature_mode == 0) k_rev_normal<<<g, kAT, 0, s>>>(P, S);
@@ -663,6 +812,27 @@ cudaError_t reverse_core(const float* post, const float* lam_post, const StepPar
 }  // namespace
 
 int adj_blocks(int nx, int ny) { return ((nx + kAT - 1) / kAT) * ny; }
+
+cudaError_t launch_step_planes(const float* post, float* dst, const StepParams& P, float* scratch, unsigned* flag,
+                               cudaStream_t s) {
+    forward_planes(post, P, scratch, s);
+    k_step_planes<<<adj_grid(P), kAT, 0, s>>>(post, dst, P, scratch, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_planes(const float* post, const StepParams& P, float* scratch, FieldOut out,
+                                 cudaStream_t s) {
+    forward_planes(post, P, scratch, s);
+    k_fields_planes<<<adj_grid(P), kAT, 0, s>>>(P, scratch, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* scratch, double* partials,
+                               cudaStream_t s) {
+    forward_planes(post, P, scratch, s);
+    k_diag_planes<<<adj_grid(P), kAT, 0, s>>>(P, scratch, partials);
+    return cudaGetLastError();
+}
 
 int adj_launches_per_step(const StepParams& P) { return P.curvature_mode == 0 ? 8 : 7; }
 

@@ -81,26 +81,8 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-
 __device__ __forceinline__ float sum9(const float (&v)[9]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-}
-
-// Segregation term of link i, w_i (s . c-hat_i) for a vector s (Eq. eq_re_color
-// with phi_i = w_i phim folded into s).
-__device__ __forceinline__ void segregation(float sx, float sy, float (&seg)[9]) {
-    seg[0] = 0.0f;
-    seg[8] = lw(8) * sx;
-    seg[4] = -seg[8];
-    seg[2] = lw(2) * sy;
-    seg[6] = -seg[2];
-    const float d1 = lw(1) * chx(1) * (sx + sy);
-    const float d3 = lw(3) * chx(1) * (sy - sx);
-    seg[1] = d1;
-    seg[5] = -d1;
-    seg[3] = d3;
-    seg[7] = -d3;
 }
 
 // ---------------------------------------------------------------------------
@@ -176,20 +158,7 @@ struct LayoutF32 {
     __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
                                                  float rr, float rb, float inv_rho, float sx, float sy,
                                                  const StepParams&) {
-        float* out = reinterpret_cast<float*>(dst) + node;
-        const bool red_major = rr >= rb;
-        const float amin = (red_major ? rb : rr) * inv_rho;
-        const float smin = red_major ? -1.0f : 1.0f;  // minority's sign of the segregation term
-        float seg[9];
-        segregation(smin * sx, smin * sy, seg);
-        float* out_min = out + (red_major ? 9 * nodes : 0);
-        float* out_maj = out + (red_major ? 0 : 9 * nodes);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float cmin = fmaf(amin, fp[i], seg[i]);
-            __stcs(out_min + i * nodes, cmin);
-            __stcs(out_maj + i * nodes, fp[i] - cmin);
-        }
+        store_recoloured_f32(reinterpret_cast<float*>(dst) + node, nodes, fp, rr, rb, inv_rho, sx, sy);
     }
 };
 
@@ -588,58 +557,8 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
                     } else {
                         nu = P.eta * inv_rho;
                     }
-                    const float lam3 = 2.0f * rcp(fmaf(6.0f, nu, 1.0f));
-                    const float a = fmaf(-0.5f, lam3, 1.0f);
-                    // correction tensor C_ab (App. A, Eq. Correction)
-                    const float qx = Gx - dPx, qy = Gy - dPy;
-                    const float iso = fmaf(ux, dPx, fmaf(uy, dPy, -rho * divu * (1.0f / 3.0f)));
-                    const float Cxx = a * fmaf(2.0f * ux, qx, -iso);
-                    const float Cyy = a * fmaf(2.0f * uy, qy, -iso);
-                    const float Cxy = a * fmaf(ux, qy, uy * qx);
-                    // modes that relax (Table 1 rows 3..8, unweighted): Pi_xx, Pi_yy, Pi_xy, N, J_x, J_y
-                    const float dsum = (f[1] + f[5]) + (f[3] + f[7]);  // diagonals
-                    const float ax = f[4] + f[8], ay = f[2] + f[6];
-                    const float pxx = dsum + ax;
-                    const float pyy = dsum + ay;
-                    const float pxy = (f[1] + f[5]) - (f[3] + f[7]);
-                    const float gN = fmaf(lg(1), dsum, fmaf(lg(2), ax + ay, f[0]));
-                    const float gJx = fmaf(lg(1), (f[1] + f[7]) - (f[3] + f[5]), lg(8) * (f[8] - f[4]));
-                    const float gJy = fmaf(lg(1), (f[1] + f[3]) - (f[5] + f[7]), lg(2) * (f[2] - f[6]));
-                    // dm = lambda (m^(0) - m) + S with the equilibria h^(p).f^(0) and
-                    // sources S^(p) of App. A (S^(1,2) = G, S^(3..5) = C)
-                    const float pres = fmaf(P.cs2_r, rr, P.cs2_b * rb);
-                    const float Neq = (P.ghost_N_mode == 0) ? fmaf(P.neq_r, rr, P.neq_b * rb) : 0.0f;
-                    const float rux = rho * ux;
-                    const float dm1 = Gx, dm2 = Gy;
-                    const float dm3 = fmaf(lam3, fmaf(rux, ux, pres) - pxx, Cxx);
-                    const float dm4 = fmaf(lam3, fmaf(rho * uy, uy, pres) - pyy, Cyy);
-                    const float dm5 = fmaf(lam3, fmaf(rux, uy, -pxy), Cxy);
-                    const float dm6 = P.lambda6 * (Neq - gN);
-                    const float dm7 = -P.lambda7 * gJx;
-                    const float dm8 = -P.lambda7 * gJy;
-                    // f+ - f = M^{-1} dm (App. A, Eq. eq84), grouped by parity of k^(p)
-                    float df[9];
-                    df[0] = fmaf(kinv(0, 3), dm3 + dm4, kinv(0, 6) * dm6);
-                    const float ex8 = fmaf(kinv(8, 3), dm3, fmaf(kinv(8, 4), dm4, kinv(8, 6) * dm6));
-                    const float ox8 = fmaf(kinv(8, 1), dm1, kinv(8, 7) * dm7);
-                    const float ey2 = fmaf(kinv(2, 3), dm3, fmaf(kinv(2, 4), dm4, kinv(2, 6) * dm6));
-                    const float oy2 = fmaf(kinv(2, 2), dm2, kinv(2, 8) * dm8);
-                    df[8] = ex8 + ox8;
-                    df[4] = ex8 - ox8;
-                    df[2] = ey2 + oy2;
-                    df[6] = ey2 - oy2;
-                    const float ed = fmaf(kinv(1, 3), dm3 + dm4, kinv(1, 6) * dm6);
-                    const float exy = kinv(1, 5) * dm5;
-                    const float odx = fmaf(kinv(1, 1), dm1, kinv(1, 7) * dm7);
-                    const float ody = fmaf(kinv(1, 2), dm2, kinv(1, 8) * dm8);
-                    const float pe = ed + exy, me = ed - exy, q1 = odx + ody, q2 = odx - ody;
-                    df[1] = pe + q1;  // (+1, +1)
-                    df[5] = pe - q1;  // (-1, -1)
-                    df[7] = me + q2;  // (+1, -1)
-                    df[3] = me - q2;  // (-1, +1)
                     float fp[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) fp[i] = f[i] + df[i];  // f+ = f + M^{-1} dm
+                    collide_increment(f, rr, rb, rho, nu, ux, uy, Gx, Gy, dPx, dPy, divu, P, fp);
                     // recolour (Eq. eq_re_color): red moves along e = grad rho^N / |grad rho^N| = -n-hat,
                     // by beta phi_i rho_R rho_B / rho (e . c-hat_i); phi_i = w_i phim for i != 0
                     const float ex = -R.B(yd, 2)[t];

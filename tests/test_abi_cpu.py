@@ -55,7 +55,7 @@ def test_defaults_are_valid(cm):
     ("lambda3_r", 2.0, "lambda3"),
     ("lambda7", 0.0, "lambda6, lambda7"),
     ("sigma", -1.0, "sigma"),
-    ("stencil_order", 6, "stencil_order"),
+    ("stencil_order", 4, "stencil_order"),
     ("precision", 3, "precision"),
     ("precision_reference", 2, "precision_reference"),
     ("visc_mode", 3, "visc_mode"),
@@ -119,3 +119,17 @@ def test_null_batch_calls(cm):
     assert lib.cmrt_batch_work_items(None) == -1
     assert lib.cmrt_batch_device_bytes(None) == 0
     lib.cmrt_batch_destroy(None)  # no-op
+
+
+def test_order6_constraints(cm):
+    p = cm.make_params({"nx": 16, "ny": 16, "stencil_order": 6})
+    assert cm.cmrt_validate(p) == cm.CMRT_OK
+    p.precision = 2
+    assert cm.cmrt_validate(p) == cm.CMRT_EINVAL and "FP32" in cm.cmrt_last_error(None)
+    q = cm.make_params({"nx": 16, "ny": 2, "stencil_order": 6, "wall_y": True})
+    assert cm.cmrt_validate(q) == cm.CMRT_EINVAL and "ny >= 3" in cm.cmrt_last_error(None)
+    q.wall_y = 0
+    assert cm.cmrt_validate(q) == cm.CMRT_OK  # periodic: the stencil wraps
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_batch_init([cm.make_params({"nx": 16, "ny": 16, "stencil_order": 6})], None, None, 0)
+    assert ei.value.status == cm.CMRT_EINVAL
