@@ -50,7 +50,7 @@ constexpr int kThreads = 128;
 constexpr int kWin = 128;
 constexpr int kHalo = 4;
 constexpr int kTileX = kWin - 2 * kHalo;  // 120
-constexpr int kRing = 8;                  // rows of post-collision populations kept in shared memory
+constexpr int kRing = 9;                  // rows of post-collision populations kept in shared memory
 
 enum class Pass : int { Step = 0, Fields = 1, Diag = 2 };
 

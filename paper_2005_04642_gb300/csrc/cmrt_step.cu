@@ -43,12 +43,35 @@ namespace cmrt {
 namespace {
 
 constexpr int kPlanes = 18;
-// ring B: grad rho^N (x, y), n-hat (x, y) over 4 rows
-constexpr int kBF = 4;
-constexpr int kBFloats = 4 * kBF * kWin;
-// ring C: G (x, y), u (x, y) over 4 rows
-constexpr int kCF = 4;
-constexpr int kCFloats = 4 * kCF * kWin;
+// Rings of stage results, each holding only the rows its readers need (a
+// row is one float per window column; fields x and y interleaved by row):
+//   grad rho^N  2 rows  (written by B at row s - 2, read by C at row s - 3)
+//   n-hat       4 rows + the mirrored row ny beyond a wall
+//   G           4 rows  (C writes row s - 3 while D may still read s - 5)
+//   u           4 rows + the mirrored row ny
+constexpr int kBFloats = (2 * 2 + 5 * 2) * kWin;  // grad rho^N, n-hat
+constexpr int kCFloats = (4 * 2 + 5 * 2) * kWin;  // G, u
+
+// The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
+// kThreads ("front") stream the rows in and run stages A-C, while the other
+// kThreads ("back") run stage D one row iteration behind them.
+constexpr int kStepThreads = 2 * kThreads;
+// Named barriers (0 is __syncthreads): the front among themselves; front ->
+// back "stage C of iteration k is in shared memory" and back -> front "stage
+// D of iteration k is done with its rows", each alternating between two ids
+// by the parity of k so that no barrier sees arrivals of two iterations.
+constexpr int kBarFront = 1;
+constexpr int kBarC = 2;  // 2, 3
+constexpr int kBarD = 4;  // 4, 5
+
+template <int ID, int N>
+__device__ __forceinline__ void bar_sync() {
+    asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "n"(N) : "memory");
+}
+template <int ID, int N>
+__device__ __forceinline__ void bar_arrive() {
+    asm volatile("bar.arrive %0, %1;\n" ::"n"(ID), "n"(N) : "memory");
+}
 
 // The reconstruction below relies on these symmetries of App. A's k vectors.
 static_assert(kinv(4, 3) == kinv(8, 3) && kinv(4, 4) == kinv(8, 4) && kinv(4, 6) == kinv(8, 6), "even x");
@@ -84,6 +107,15 @@ __device__ __forceinline__ int wrap(int v, int n) {
 __device__ __forceinline__ float sum9(const float (&v)[9]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
 }
+// (sum9(r), sum9(b)) in the same order, as packed FP32x2 adds (one instruction per pair)
+__device__ __forceinline__ float2 sum9x2(const float (&r)[9], const float (&b)[9]) {
+    float2 v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = make_float2(r[i], b[i]);
+    const float2 a = __fadd2_rn(__fadd2_rn(v[0], v[1]), __fadd2_rn(v[2], v[3]));
+    const float2 c = __fadd2_rn(__fadd2_rn(v[4], v[5]), __fadd2_rn(v[6], v[7]));
+    return __fadd2_rn(__fadd2_rn(a, c), v[8]);
+}
 
 // ---------------------------------------------------------------------------
 // Storage layouts.  A layout fixes the bytes of one ring row, how a thread
@@ -95,7 +127,6 @@ __device__ __forceinline__ float sum9(const float (&v)[9]) {
 // 32-bit: 18 FP32 planes.
 struct LayoutF32 {
     static constexpr int kSlotBytes = kPlanes * kWin * 4;
-    static constexpr bool kSplitA = false;  // ring A keeps the red fraction for stage D
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
     static constexpr size_t node_bytes() { return kPlanes * 4; }
@@ -168,7 +199,6 @@ struct Layout16 {
     static constexpr int kRhoBytes = kWin * 8;  // float2 (rho_R, rho_B) per column
     static constexpr int kDevBytes = kWin * 4;  // one 16-bit pair per column and link
     static constexpr int kSlotBytes = kRhoBytes + 9 * kDevBytes;
-    static constexpr bool kSplitA = true;  // smaller ring A, stage D recomputes rho^N
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
     static constexpr size_t node_bytes() { return 8 + 9 * 4; }
@@ -295,62 +325,80 @@ using LayoutB16 = Layout16<__nv_bfloat162>;
 template <class L>
 struct Geometry {
     static constexpr int kPopBytes = kRing * L::kSlotBytes;
-    // ring A: without kSplitA, chi_R, Phi', rho, j_x, j_y over 8 rows; with it,
-    // Phi' over 8 rows (ring Q) and chi_R, rho, j_x, j_y over 4 rows
-    static constexpr int kQFloats = L::kSplitA ? 8 * kWin : 0;
-    static constexpr int kAFloats = L::kSplitA ? 4 * 4 * kWin : 8 * 5 * kWin;
+    // ring A: Phi' over 8 rows (ring Q; D's stencil reads it) and chi_R, rho,
+    // j_x, j_y over 4 rows (B and C read them; D recomputes rho^N)
+    static constexpr int kQFloats = 8 * kWin;
+    static constexpr int kAFloats = 4 * 4 * kWin;
     static constexpr int kBytes = kPopBytes + 4 * (kQFloats + kAFloats + kBFloats + kCFloats);
 };
 
-template <class L>
+// two warp-specialised CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA, 16 B of static
+// shared memory in the batched kernel)
+static_assert(2 * (Geometry<LayoutF32>::kBytes + 1024 + 16) <= 228 * 1024, "two FP32 step CTAs per SM");
+
+template <class L, bool W>
 struct Rings {
     char* pop;
     float* q;
     float* a;
     float* b;
     float* c;
-    __device__ __forceinline__ const char* slot(int row) const { return pop + (row & (kRing - 1)) * L::kSlotBytes; }
+    int ghost;  // ny with walls W (n-hat and u keep the mirrored row ny in slot 4)
+    // population ring slot k (rows map to slots in order of arrival)
+    __device__ __forceinline__ const char* slot(int k) const { return pop + k * L::kSlotBytes; }
     // ring A fields: the red fraction chi_R = a / (a + b) (a = rho_R / rho0_r,
     // b = rho_B / rho0_b; rho^N = 2 chi_R - 1, Eq. equ_rhoN_def)
-    __device__ __forceinline__ float* chiR(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 0) * kWin : a + ((row & 7) * 5 + 0) * kWin;
-    }
-    __device__ __forceinline__ float* phip(int row) const {
-        return L::kSplitA ? q + (row & 7) * kWin : a + ((row & 7) * 5 + 1) * kWin;
-    }
-    __device__ __forceinline__ float* rho(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 1) * kWin : a + ((row & 7) * 5 + 2) * kWin;
-    }
-    __device__ __forceinline__ float* jx(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 2) * kWin : a + ((row & 7) * 5 + 3) * kWin;
-    }
-    __device__ __forceinline__ float* jy(int row) const {
-        return L::kSplitA ? a + ((row & 3) * 4 + 3) * kWin : a + ((row & 7) * 5 + 4) * kWin;
-    }
-    __device__ __forceinline__ float* B(int row, int f) const { return b + (((row & 3) * kBF) + f) * kWin; }
-    __device__ __forceinline__ float* C(int row, int f) const { return c + (((row & 3) * kCF) + f) * kWin; }
+    __device__ __forceinline__ float* chiR(int row) const { return a + ((row & 3) * 4 + 0) * kWin; }
+    __device__ __forceinline__ float* phip(int row) const { return q + (row & 7) * kWin; }
+    __device__ __forceinline__ float* rho(int row) const { return a + ((row & 3) * 4 + 1) * kWin; }
+    __device__ __forceinline__ float* jx(int row) const { return a + ((row & 3) * 4 + 2) * kWin; }
+    __device__ __forceinline__ float* jy(int row) const { return a + ((row & 3) * 4 + 3) * kWin; }
+    __device__ __forceinline__ int slot4(int row) const { return (W && row == ghost) ? 4 : (row & 3); }
+    __device__ __forceinline__ float* grad(int row, int f) const { return b + ((row & 1) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* nh(int row, int f) const { return b + (4 + slot4(row) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* G(int row, int f) const { return c + ((row & 3) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* u(int row, int f) const { return c + (8 + slot4(row) * 2 + f) * kWin; }
 };
+
+// The rings carved out of a CTA's dynamic shared memory.
+template <class L, bool W>
+__device__ __forceinline__ Rings<L, W> make_rings(char* smem, int ny) {
+    using G = Geometry<L>;
+    Rings<L, W> R;
+    R.pop = smem;
+    R.q = reinterpret_cast<float*>(smem + G::kPopBytes);
+    R.a = R.q + G::kQFloats;
+    R.b = R.a + G::kAFloats;
+    R.c = R.b + kBFloats;
+    R.ghost = ny;
+    return R;
+}
 
 // Pre-collision populations at (row y, window column t): pull from the
 // post-collision ring, f_i(r) = P_i(r - c_i) (Eq. equ_evolution), with
 // half-way bounce-back P_opp(i)(r) where r - c_i lies beyond a wall.
 // With PRE the rows hold pre-collision populations f(t) already in place
 // (the public FP32 layout), so the node's own column is read unshifted.
+// The ring slots of rows y - 1, y and y + 1 are passed in.
 template <class L, bool WALLS, bool PRE>
-__device__ __forceinline__ void gather(const Rings<L>& R, int y, int t, int ny, const StepParams& P,
-                                       float (&fr)[9], float (&fb)[9]) {
+__device__ __forceinline__ void gather(const char* below, const char* mid, const char* above, int y, int t, int ny,
+                                       const StepParams& P, float (&fr)[9], float (&fb)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sy = y - lcy(i);
         if (PRE) {
-            L::pair(R.slot(y), i, t, P, fr[i], fb[i]);
+            L::pair(mid, i, t, P, fr[i], fb[i]);
         } else if (WALLS && (sy < 0 || sy >= ny)) {
-            L::pair(R.slot(y), lopp(i), t, P, fr[i], fb[i]);
+            L::pair(mid, lopp(i), t, P, fr[i], fb[i]);
         } else {
-            L::pair(R.slot(sy), i, t - lcx(i), P, fr[i], fb[i]);
+            L::pair(lcy(i) > 0 ? below : (lcy(i) < 0 ? above : mid), i, t - lcx(i), P, fr[i], fb[i]);
         }
     }
 }
+
+// slot of the row d rows before the row in slot k of a kRing-slot ring (0 <= d < kRing)
+__device__ __forceinline__ int ring_back(int k, int d) { return k >= d ? k - d : k - d + kRing; }
+__device__ __forceinline__ int ring_next(int k) { return k == kRing - 1 ? 0 : k + 1; }
 
 // Compact derivatives of a ring field around (row y, column t).
 template <typename Row>
@@ -371,6 +419,14 @@ template <class L>
 constexpr int min_ctas_per_sm() {
     return Geometry<L>::kBytes + 1024 <= 228 * 1024 / 3 ? 3 : 2;
 }
+// CTA size of a pass: the step is warp-specialised (front + back)
+constexpr int pass_threads(Pass m) { return m == Pass::Step ? kStepThreads : kThreads; }
+// resident CTAs per SM a pass is compiled for: the warp-specialised step
+// keeps two CTAs (16 warps) per SM in every storage form
+template <class L>
+constexpr int pass_ctas_per_sm(Pass m) {
+    return m == Pass::Step ? 2 : min_ctas_per_sm<L>();
+}
 
 // Diagnostics accumulators of one thread (Pass::Diag).
 struct DiagAcc {
@@ -379,12 +435,29 @@ struct DiagAcc {
 
 // One tile: the strip [x0, x0 + 120) of rows [y0, y0 + rows) of a lattice,
 // with its whole four-stage row pipeline.  Leaves no copy in flight.
+//
+// Row iteration k (s = y0 - 4 + k) runs stage A at row s - 1, B at s - 2, C
+// at s - 3 and D at s - 4; the copy of row s + 2 is issued at its start, into
+// the ring slot of row s - 7.  The fields and diagnostics passes run all four
+// stages in every thread of a 128-thread CTA, one barrier between stages.
+// The step is warp-specialised (2 x 128 threads): the front threads wait for
+// the copies, issue the next one and run A, B and C of iteration k, then
+// publish them with bar.arrive; the back threads run D of iteration k while
+// the front is at iteration k + 1, reading population rows s - 5 .. s - 3
+// (nine rows in flight in all: D's three, A's three, two copies and the row
+// D of iteration k - 1 read).  Before leaving iteration k the front waits
+// for D of iteration k - 1, so that in iteration k + 1 nothing it writes --
+// ring A row s, grad rho^N and n-hat rows s - 1, G and u rows s - 2, the
+// copy into the slot of row s - 6 -- is still being read; the mirrored wall
+// rows ny of n-hat and u have slots of their own.
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
-__device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop_addr, const char* __restrict__ src,
+__device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsigned pop_addr, const char* __restrict__ src,
                                            char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
                                            const int rows, const FieldOut& fo, unsigned* __restrict__ flag,
                                            DiagAcc& acc) {
-    const int t = threadIdx.x;
+    constexpr bool kWS = MODE == Pass::Step;
+    const bool front = !kWS || threadIdx.x < kThreads;  // warp-uniform
+    const int t = front ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) - kThreads;
     const int nx = P.nx, ny = P.ny;
     const size_t nodes = static_cast<size_t>(nx) * ny;
     const int y_end = min(y0 + rows, ny);
@@ -395,215 +468,252 @@ __device__ __forceinline__ void chain_tile(const Rings<L>& R, const unsigned pop
 
     typename L::template Plan<VEC> plan;
     plan.init(x0, nx, nodes);
-    auto issue_row = [&](int row) {
-        plan.issue(pop_addr + static_cast<unsigned>((row & (kRing - 1)) * L::kSlotBytes), src, wrap(row, ny), nx);
+    // population rows go to ring slots in order: row s_first + j to slot j mod kRing
+    auto issue_row = [&](int row, int slot) {
+        int gy = row;  // periodic image of the row (the modulo only near the lattice's ends)
+        if (gy < 0 || gy >= ny) gy = wrap(gy, ny);
+        plan.issue(pop_addr + static_cast<unsigned>(slot * L::kSlotBytes), src, gy, nx);
     };
 
-    if (row_ok(s_first)) issue_row(s_first);
-    cp_commit();
-    if (row_ok(s_first + 1)) issue_row(s_first + 1);
-    cp_commit();
-
-    for (int k = 0; k < iters; ++k) {
-        const int s = s_first + k;
-        cp_wait<1>();
-        __syncthreads();
-        if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2);
-        cp_commit();
-
-        // ---------------- stage A: moments at row ya = s - 1 (tile + 3 halo)
-        {
-            const int ya = s - 1;
-            if (ya >= y0 - 3 && ya <= y_end + 2 && row_ok(ya) && t >= 1 && t < kWin - 1) {
-                float fr[9], fb[9];
-                gather<L, WALLS, PRE>(R, ya, t, ny, P, fr, fb);
-                const float rr = sum9(fr);
-                const float rb = sum9(fb);
-                // colour-blind momentum sum_i f_i c_i (Eq. equ_u_def)
-                const float jx = ((fr[1] + fb[1]) + (fr[7] + fb[7])) + (fr[8] + fb[8]) -
-                                 (((fr[3] + fb[3]) + (fr[5] + fb[5])) + (fr[4] + fb[4]));
-                const float jy = ((fr[1] + fb[1]) + (fr[3] + fb[3])) + (fr[2] + fb[2]) -
-                                 (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
-                const float a = rr * P.inv_rho0_r;
-                const float b = rb * P.inv_rho0_b;
-                // red fraction: rho^N = 2 chi_R - 1 (Eq. equ_rhoN_def); near pure
-                // blue chi_R is small and keeps the digits that rho^N, stored in
-                // FP32 next to -1, would lose
-                const float inv_ab = rcp(a + b);
-                const float chr = a * inv_ab;
-                const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
-                R.chiR(ya)[t] = chr;
-                R.phip(ya)[t] = phip;
-                R.rho(ya)[t] = rr + rb;
-                R.jx(ya)[t] = jx;
-                R.jy(ya)[t] = jy;
-                if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
-                    R.chiR(-1)[t] = chr;
-                    R.phip(-1)[t] = phip;
-                }
-                if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
-                    R.chiR(ny)[t] = chr;
-                    R.phip(ny)[t] = phip;
-                }
+    // ---------------- stage A: moments at row ya = s - 1 (tile + 3 halo); ks = slot of row s
+    auto stage_a = [&](const int s, const int ks) {
+        const int ya = s - 1;
+        if (ya >= y0 - 3 && ya <= y_end + 2 && row_ok(ya) && t >= 1 && t < kWin - 1) {
+            float fr[9], fb[9];
+            gather<L, WALLS, PRE>(R.slot(ring_back(ks, 2)), R.slot(ring_back(ks, 1)), R.slot(ks), ya, t, ny, P, fr,
+                                  fb);
+            const float2 rrb = sum9x2(fr, fb);
+            const float rr = rrb.x, rb = rrb.y;
+            // colour-blind momentum sum_i f_i c_i (Eq. equ_u_def)
+            const float jx = ((fr[1] + fb[1]) + (fr[7] + fb[7])) + (fr[8] + fb[8]) -
+                             (((fr[3] + fb[3]) + (fr[5] + fb[5])) + (fr[4] + fb[4]));
+            const float jy = ((fr[1] + fb[1]) + (fr[3] + fb[3])) + (fr[2] + fb[2]) -
+                             (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
+            const float a = rr * P.inv_rho0_r;
+            const float b = rb * P.inv_rho0_b;
+            // red fraction: rho^N = 2 chi_R - 1 (Eq. equ_rhoN_def); near pure
+            // blue chi_R is small and keeps the digits that rho^N, stored in
+            // FP32 next to -1, would lose
+            const float inv_ab = rcp(a + b);
+            const float chr = a * inv_ab;
+            const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
+            R.chiR(ya)[t] = chr;
+            R.phip(ya)[t] = phip;
+            R.rho(ya)[t] = rr + rb;
+            R.jx(ya)[t] = jx;
+            R.jy(ya)[t] = jy;
+            if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
+                R.chiR(-1)[t] = chr;
+                R.phip(-1)[t] = phip;
+            }
+            if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
+                R.chiR(ny)[t] = chr;
+                R.phip(ny)[t] = phip;
             }
         }
-        __syncthreads();
-
-        // ---------------- stage B: grad rho^N, n-hat at row yb = s - 2 (tile + 2)
-        {
-            const int yb = s - 2;
-            if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-                // grad rho^N = 2 grad chi_R (the stencil weights sum to zero)
-                auto ch_row = [&](int r) { return R.chiR(r); };
-                const float sgn = 2.0f;
-                const float gx = sgn * ddx_at(ch_row, yb, t);
-                const float gy = sgn * ddy_at(ch_row, yb, t);
-                // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
-                const float mag2 = fmaf(gx, gx, gy * gy);
-                const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
-                const float nhx = -gx * inv;
-                const float nhy = -gy * inv;
-                R.B(yb, 0)[t] = gx;
-                R.B(yb, 1)[t] = gy;
-                R.B(yb, 2)[t] = nhx;
-                R.B(yb, 3)[t] = nhy;
-                if (WALLS && yb == 0) {  // reflected normal beyond the wall
-                    R.B(-1, 2)[t] = nhx;
-                    R.B(-1, 3)[t] = -nhy;
-                }
-                if (WALLS && yb == ny - 1) {
-                    R.B(ny, 2)[t] = nhx;
-                    R.B(ny, 3)[t] = -nhy;
-                }
+    };
+    // ---------------- stage B: grad rho^N, n-hat at row yb = s - 2 (tile + 2)
+    auto stage_b = [&](const int s) {
+        const int yb = s - 2;
+        if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
+            // grad rho^N = 2 grad chi_R (the stencil weights sum to zero)
+            auto ch_row = [&](int r) { return R.chiR(r); };
+            const float gx = 2.0f * ddx_at(ch_row, yb, t);
+            const float gy = 2.0f * ddy_at(ch_row, yb, t);
+            // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
+            const float mag2 = fmaf(gx, gx, gy * gy);
+            const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+            const float nhx = -gx * inv;
+            const float nhy = -gy * inv;
+            R.grad(yb, 0)[t] = gx;
+            R.grad(yb, 1)[t] = gy;
+            R.nh(yb, 0)[t] = nhx;
+            R.nh(yb, 1)[t] = nhy;
+            if (WALLS && yb == 0) {  // reflected normal beyond the wall
+                R.nh(-1, 0)[t] = nhx;
+                R.nh(-1, 1)[t] = -nhy;
+            }
+            if (WALLS && yb == ny - 1) {
+                R.nh(ny, 0)[t] = nhx;
+                R.nh(ny, 1)[t] = -nhy;
             }
         }
-        __syncthreads();
-
-        // ---------------- stage C: curvature, force, velocity at row yc = s - 3 (tile + 1)
-        {
-            const int yc = s - 3;
-            if (yc >= y0 - 1 && yc <= y_end && row_ok(yc) && t >= 3 && t < kWin - 3) {
-                float K;
-                if (P.curvature_mode == 0) {
-                    // K = div n-hat (Sec. 2)
-                    K = ddx_at([&](int r) { return R.B(r, 2); }, yc, t) + ddy_at([&](int r) { return R.B(r, 3); }, yc, t);
-                } else {
-                    K = P.fixed_K;
-                }
-                const float gx = R.B(yc, 0)[t];
-                const float gy = R.B(yc, 1)[t];
-                const float rho = R.rho(yc)[t];
-                // G = sigma K grad rho^N / 2 + rho g_acc + g_vol (Eq. equ_stforce plus body force)
-                const float hk = P.half_sigma * K;
-                const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
-                const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
-                const float inv_rho = rcp(rho);
-                // force-adjusted velocity (Eq. equ_u_def)
-                const float ux = fmaf(0.5f, Gx, R.jx(yc)[t]) * inv_rho;
-                const float uy = fmaf(0.5f, Gy, R.jy(yc)[t]) * inv_rho;
-                R.C(yc, 0)[t] = Gx;
-                R.C(yc, 1)[t] = Gy;
-                R.C(yc, 2)[t] = ux;
-                R.C(yc, 3)[t] = uy;
-                if (WALLS && yc == 0) {  // no-slip: odd mirror of u
-                    R.C(-1, 2)[t] = -ux;
-                    R.C(-1, 3)[t] = -uy;
-                }
-                if (WALLS && yc == ny - 1) {
-                    R.C(ny, 2)[t] = -ux;
-                    R.C(ny, 3)[t] = -uy;
-                }
+    };
+    // ---------------- stage C: curvature, force, velocity at row yc = s - 3 (tile + 1)
+    auto stage_c = [&](const int s) {
+        const int yc = s - 3;
+        if (yc >= y0 - 1 && yc <= y_end && row_ok(yc) && t >= 3 && t < kWin - 3) {
+            float K;
+            if (P.curvature_mode == 0) {
+                // K = div n-hat (Sec. 2)
+                K = ddx_at([&](int r) { return R.nh(r, 0); }, yc, t) + ddy_at([&](int r) { return R.nh(r, 1); }, yc, t);
+            } else {
+                K = P.fixed_K;
+            }
+            const float gx = R.grad(yc, 0)[t];
+            const float gy = R.grad(yc, 1)[t];
+            const float rho = R.rho(yc)[t];
+            // G = sigma K grad rho^N / 2 + rho g_acc + g_vol (Eq. equ_stforce plus body force)
+            const float hk = P.half_sigma * K;
+            const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
+            const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
+            const float inv_rho = rcp(rho);
+            // force-adjusted velocity (Eq. equ_u_def)
+            const float ux = fmaf(0.5f, Gx, R.jx(yc)[t]) * inv_rho;
+            const float uy = fmaf(0.5f, Gy, R.jy(yc)[t]) * inv_rho;
+            R.G(yc, 0)[t] = Gx;
+            R.G(yc, 1)[t] = Gy;
+            R.u(yc, 0)[t] = ux;
+            R.u(yc, 1)[t] = uy;
+            if (WALLS && yc == 0) {  // no-slip: odd mirror of u
+                R.u(-1, 0)[t] = -ux;
+                R.u(-1, 1)[t] = -uy;
+            }
+            if (WALLS && yc == ny - 1) {
+                R.u(ny, 0)[t] = -ux;
+                R.u(ny, 1)[t] = -uy;
             }
         }
-        __syncthreads();
-
-        // ---------------- stage D: collide, recolour, store at row yd = s - 4 (tile)
-        {
-            const int yd = s - 4;
-            const int gxo = x0 + t - kHalo;
-            if (yd >= y0 && yd < y_end && t >= kHalo && t < kWin - kHalo && gxo < nx) {
-                float fr[9], fb[9], f[9];
-                gather<L, WALLS, PRE>(R, yd, t, ny, P, fr, fb);
-                const float rr = sum9(fr);
-                const float rb = sum9(fb);
+    };
+    // ---------------- stage D: collide, recolour, store at row yd = s - 4 (tile); ks = slot of row s
+    auto stage_d = [&](const int s, const int ks) {
+        const int yd = s - 4;
+        const int gxo = x0 + t - kHalo;
+        if (yd >= y0 && yd < y_end && t >= kHalo && t < kWin - kHalo && gxo < nx) {
+            float fr[9], fb[9], f[9];
+            gather<L, WALLS, PRE>(R.slot(ring_back(ks, 5)), R.slot(ring_back(ks, 4)), R.slot(ring_back(ks, 3)), yd,
+                                  t, ny, P, fr, fb);
+            const float2 rrb = sum9x2(fr, fb);
+            const float rr = rrb.x, rb = rrb.y;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
-                const float rho = rr + rb;
-                const float ux = R.C(yd, 2)[t];
-                const float uy = R.C(yd, 3)[t];
-                if (MODE == Pass::Step) {
-                    if (!isfinite(rho)) atomicOr(flag, 1u);
-                    const float Gx = R.C(yd, 0)[t];
-                    const float Gy = R.C(yd, 1)[t];
-                    auto phip_row = [&](int r) { return R.phip(r); };
-                    const float dPx = ddx_at(phip_row, yd, t);
-                    const float dPy = ddy_at(phip_row, yd, t);
-                    const float divu = ddx_at([&](int r) { return R.C(r, 2); }, yd, t) +
-                                       ddy_at([&](int r) { return R.C(r, 3); }, yd, t);
-                    const float inv_rho = rcp(rho);
-                    // local shear eigenvalue (Sec. 2: nu(rho^N) = (2/lambda_3 - 1)/6)
-                    float nu;
-                    if (P.visc_mode == 0) {
-                        float rn;
-                        if (L::kSplitA) {
-                            // rho^N of this node (Eq. equ_rhoN_def); the 4-row ring A may
-                            // already hold a wall's ghost row in row yd's slot
-                            const float ra = rr * P.inv_rho0_r, ba = rb * P.inv_rho0_b;
-                            rn = (ra - ba) * rcp(ra + ba);
-                        } else {
-                            rn = fmaf(2.0f, R.chiR(yd)[t], -1.0f);  // only sets nu: no cancellation concern
-                        }
-                        nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
-                    } else {
-                        nu = P.eta * inv_rho;
-                    }
-                    float fp[9];
-                    collide_increment(f, rr, rb, rho, nu, ux, uy, Gx, Gy, dPx, dPy, divu, P, fp);
-                    // recolour (Eq. eq_re_color): red moves along e = grad rho^N / |grad rho^N| = -n-hat,
-                    // by beta phi_i rho_R rho_B / rho (e . c-hat_i); phi_i = w_i phim for i != 0
-                    const float ex = -R.B(yd, 2)[t];
-                    const float ey = -R.B(yd, 3)[t];
-                    const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
-                    const float sg = P.beta * (rr * rb) * inv_rho * phim;
-                    L::store(dst, nodes, static_cast<size_t>(yd) * nx + gxo, fp, rr, rb, inv_rho, sg * ex, sg * ey, P);
-                } else if (MODE == Pass::Fields) {
-                    const size_t o = static_cast<size_t>(yd) * nx + gxo;
-                    if (fo.rho_r) fo.rho_r[o] = rr;
-                    if (fo.rho_b) fo.rho_b[o] = rb;
-                    if (fo.ux) fo.ux[o] = ux;
-                    if (fo.uy) fo.uy[o] = uy;
-                    if (fo.p) fo.p[o] = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+            for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
+            const float rho = rr + rb;
+            const float ux = R.u(yd, 0)[t];
+            const float uy = R.u(yd, 1)[t];
+            if (MODE == Pass::Step) {
+                if (!isfinite(rho)) atomicOr(flag, 1u);
+                const float Gx = R.G(yd, 0)[t];
+                const float Gy = R.G(yd, 1)[t];
+                auto phip_row = [&](int r) { return R.phip(r); };
+                const float dPx = ddx_at(phip_row, yd, t);
+                const float dPy = ddy_at(phip_row, yd, t);
+                const float divu = ddx_at([&](int r) { return R.u(r, 0); }, yd, t) +
+                                   ddy_at([&](int r) { return R.u(r, 1); }, yd, t);
+                const float inv_rho = rcp(rho);
+                // local shear eigenvalue (Sec. 2: nu(rho^N) = (2/lambda_3 - 1)/6)
+                float nu;
+                if (P.visc_mode == 0) {
+                    // rho^N of this node (Eq. equ_rhoN_def): ring A's four rows no longer hold row yd
+                    const float ra = rr * P.inv_rho0_r, ba = rb * P.inv_rho0_b;
+                    const float rn = (ra - ba) * rcp(ra + ba);
+                    nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
                 } else {
-                    const float jx = (f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]);
-                    const float jy = (f[1] + f[2] + f[3]) - (f[5] + f[6] + f[7]);
-                    if (isfinite(rho)) {
-                        acc.r += rr;
-                        acc.b += rb;
-                        acc.jx += jx;
-                        acc.jy += jy;
-                        acc.u2 = fmax(acc.u2, static_cast<double>(ux) * ux + static_cast<double>(uy) * uy);
-                    } else {
-                        acc.bad += 1.0;
-                    }
+                    nu = P.eta * inv_rho;
                 }
+                float fp[9];
+                collide_increment(f, rr, rb, rho, nu, ux, uy, Gx, Gy, dPx, dPy, divu, P, fp);
+                // recolour (Eq. eq_re_color): red moves along e = grad rho^N / |grad rho^N| = -n-hat,
+                // by beta phi_i rho_R rho_B / rho (e . c-hat_i); phi_i = w_i phim for i != 0
+                const float ex = -R.nh(yd, 0)[t];
+                const float ey = -R.nh(yd, 1)[t];
+                const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
+                const float sg = P.beta * (rr * rb) * inv_rho * phim;
+                L::store(dst, nodes, static_cast<size_t>(yd) * nx + gxo, fp, rr, rb, inv_rho, sg * ex, sg * ey, P);
+            } else if (MODE == Pass::Fields) {
+                const size_t o = static_cast<size_t>(yd) * nx + gxo;
+                if (fo.rho_r) fo.rho_r[o] = rr;
+                if (fo.rho_b) fo.rho_b[o] = rb;
+                if (fo.ux) fo.ux[o] = ux;
+                if (fo.uy) fo.uy[o] = uy;
+                if (fo.p) fo.p[o] = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+            } else {
+                const float jx = (f[1] + f[7] + f[8]) - (f[3] + f[4] + f[5]);
+                const float jy = (f[1] + f[2] + f[3]) - (f[5] + f[6] + f[7]);
+                if (isfinite(rho)) {
+                    acc.r += rr;
+                    acc.b += rb;
+                    acc.jx += jx;
+                    acc.jy += jy;
+                    acc.u2 = fmax(acc.u2, static_cast<double>(ux) * ux + static_cast<double>(uy) * uy);
+                } else {
+                    acc.bad += 1.0;
+                }
+            }
+        }
+    };
+
+    // the first two rows, into slots 0 and 1
+    auto issue_first = [&]() {
+        if (row_ok(s_first)) issue_row(s_first, 0);
+        cp_commit();
+        if (row_ok(s_first + 1)) issue_row(s_first + 1, 1);
+        cp_commit();
+    };
+    if (!kWS) {
+        issue_first();
+        int ks = 0;  // slot of row s
+        for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
+            const int s = s_first + k;
+            cp_wait<1>();
+            __syncthreads();
+            if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2, ring_next(ring_next(ks)));
+            cp_commit();
+            stage_a(s, ks);
+            __syncthreads();
+            stage_b(s);
+            __syncthreads();
+            stage_c(s);
+            __syncthreads();
+            stage_d(s, ks);
+        }
+        cp_wait<0>();
+    } else if (front) {
+        issue_first();
+        int ks = 0;
+        for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
+            const int s = s_first + k;
+            cp_wait<1>();
+            bar_sync<kBarFront, kThreads>();
+            // row s + 2 goes to the slot of row s - 7, last read by D of iteration k - 2
+            if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2, ring_next(ring_next(ks)));
+            cp_commit();
+            stage_a(s, ks);
+            bar_sync<kBarFront, kThreads>();
+            stage_b(s);
+            bar_sync<kBarFront, kThreads>();
+            stage_c(s);
+            // publish A-C of iteration k, then wait until D of iteration k - 1
+            // is done with the rows that iteration k + 1 overwrites
+            if (k & 1) {
+                bar_arrive<kBarC + 1, kStepThreads>();
+                bar_sync<kBarD + 1, kStepThreads>();
+            } else {
+                bar_arrive<kBarC, kStepThreads>();
+                bar_sync<kBarD, kStepThreads>();
+            }
+        }
+        cp_wait<0>();
+    } else {
+        bar_arrive<kBarD, kStepThreads>();  // no D before iteration 0
+        int ks = 0;
+        for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
+            if (k & 1) bar_sync<kBarC + 1, kStepThreads>();
+            else bar_sync<kBarC, kStepThreads>();
+            stage_d(s_first + k, ks);
+            if (k + 1 < iters) {
+                if (k & 1) bar_arrive<kBarD, kStepThreads>();  // D of iteration k + 1 (even) may follow
+                else bar_arrive<kBarD + 1, kStepThreads>();
             }
         }
     }
-    cp_wait<0>();
 }
 
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
-__global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>())
+__global__ void __launch_bounds__(pass_threads(MODE), pass_ctas_per_sm<L>(MODE))
     k_chain(const char* __restrict__ src, char* __restrict__ dst, const StepParams P, const int rows, FieldOut fo,
             unsigned* __restrict__ flag, double* __restrict__ partials) {
-    using G = Geometry<L>;
     extern __shared__ __align__(16) char smem[];
-    Rings<L> R;
-    R.pop = smem;
-    R.q = reinterpret_cast<float*>(smem + G::kPopBytes);
-    R.a = R.q + G::kQFloats;
-    R.b = R.a + G::kAFloats;
-    R.c = R.b + kBFloats;
+    const Rings<L, WALLS> R = make_rings<L, WALLS>(smem, P.ny);
     const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
 
     DiagAcc acc;
@@ -649,16 +759,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>())
 // the items, and the last CTA to leave resets the counters for the next
 // launch.
 template <class L, bool VEC>
-__global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>()) k_batch(const BatchArgs A) {
-    using G = Geometry<L>;
+__global__ void __launch_bounds__(kStepThreads, pass_ctas_per_sm<L>(Pass::Step)) k_batch(const BatchArgs A) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_item;
-    Rings<L> R;
-    R.pop = smem;
-    R.q = reinterpret_cast<float*>(smem + G::kPopBytes);
-    R.a = R.q + G::kQFloats;
-    R.b = R.a + G::kAFloats;
-    R.c = R.b + kBFloats;
     const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     for (;;) {
         __syncthreads();  // the previous item is done with the rings and s_item
@@ -671,10 +774,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas_per_sm<L>()) k_batch(const 
         const size_t off = A.offsets[w.member];
         DiagAcc acc;
         if (P.wall_y)
-            chain_tile<L, VEC, true, Pass::Step, false>(R, pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0, w.rows,
+            chain_tile<L, VEC, true, Pass::Step, false>(make_rings<L, true>(smem, P.ny), pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0, w.rows,
                                                         FieldOut{}, A.flags + w.member, acc);
         else
-            chain_tile<L, VEC, false, Pass::Step, false>(R, pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0,
+            chain_tile<L, VEC, false, Pass::Step, false>(make_rings<L, false>(smem, P.ny), pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0,
                                                          w.rows, FieldOut{}, A.flags + w.member, acc);
     }
     if (threadIdx.x == 0) {
@@ -699,13 +802,14 @@ cudaError_t batch_configure(int dev, int* ctas_per_sm) {
         configured |= bit;
     }
     if (ctas_per_sm)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_batch<L, VEC>, kThreads, Geometry<L>::kBytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_batch<L, VEC>, kStepThreads,
+                                                          Geometry<L>::kBytes);
     return e;
 }
 
 template <class L, bool VEC>
 cudaError_t batch_launch(const BatchArgs& A, int grid, cudaStream_t s) {
-    k_batch<L, VEC><<<grid, kThreads, Geometry<L>::kBytes, s>>>(A);
+    k_batch<L, VEC><<<grid, kStepThreads, Geometry<L>::kBytes, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -758,7 +862,7 @@ cudaError_t launch_one(const void* src, void* dst, const StepParams& P, int rows
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    k_chain<L, VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), kThreads, smem, s>>>(
+    k_chain<L, VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), pass_threads(MODE), smem, s>>>(
         static_cast<const char*>(src), static_cast<char*>(dst), P, rows, fo, flag, partials);
     return cudaGetLastError();
 }
@@ -799,7 +903,8 @@ int chain_rows(int nx, int ny, int sms, int precision) {
     // pipeline), and the CTAs run in waves of (SMs x resident CTAs); pick
     // the segment length that minimises waves x (rows + 8).
     const int strips = (nx + kTileX - 1) / kTileX;
-    const int per_sm = precision == kPrecF32 ? min_ctas_per_sm<LayoutF32>() : min_ctas_per_sm<LayoutF16>();
+    const int per_sm = precision == kPrecF32 ? pass_ctas_per_sm<LayoutF32>(Pass::Step)
+                                             : pass_ctas_per_sm<LayoutF16>(Pass::Step);
     const long slots = static_cast<long>(per_sm) * (sms > 0 ? sms : 1);
     int best = 8;
     long best_cost = -1;
