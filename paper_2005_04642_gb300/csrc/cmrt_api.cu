@@ -49,8 +49,18 @@ struct Ctx {
     float* adj_lam[2] = {nullptr, nullptr};
     float* adj_ckpt = nullptr;           // checkpoints, float[cap][18][n]
     size_t adj_ckpt_cap = 0;
-    float* adj_seg = nullptr;            // recomputed segment states, float[cap][18][n]
+    float* adj_seg = nullptr;            // segment states (slot 0: the checkpoint), float[cap][18][n]
     size_t adj_seg_cap = 0;
+    // CUDA graphs of one checkpoint segment (replay + reverse steps), keyed by
+    // the segment length and the adjoint buffer it starts from; recorded on a
+    // private stream and valid while the workspace pointers stay put
+    struct AdjGraph {
+        int64_t len;
+        int a;
+        cudaGraphExec_t exec;
+    };
+    std::vector<AdjGraph> adj_graphs;
+    cudaStream_t adj_capture = nullptr;
     size_t adj_bytes = 0;
     int rows = 128;                      // rows per CTA of the chain kernel
     int64_t t = 0;
@@ -300,6 +310,12 @@ cmrt_status set_device(Ctx* c) {
     return CMRT_OK;
 }
 
+void drop_adj_graphs(Ctx* c) {
+    for (Ctx::AdjGraph& g : c->adj_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->adj_graphs.clear();
+}
+
 void free_all(Ctx* c) {
     if (!c->owner) {  // a member view borrows its state and flag from the batch
         for (void*& b : c->buf)
@@ -318,6 +334,8 @@ void free_all(Ctx* c) {
     if (c->adj_seg) cudaFree(c->adj_seg), c->adj_seg = nullptr;
     c->adj_bytes = 0;
     c->adj_ckpt_cap = c->adj_seg_cap = 0;
+    drop_adj_graphs(c);
+    if (c->adj_capture) cudaStreamDestroy(c->adj_capture), c->adj_capture = nullptr;
 }
 
 cmrt_status check_flag(Ctx* c) {
@@ -1416,6 +1434,7 @@ cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
     }
     if (seg > c->adj_seg_cap) {
         CK(c, cudaStreamSynchronize(c->stream));
+        drop_adj_graphs(c);  // they name the old segment buffer
         if (c->adj_seg) cudaFree(c->adj_seg), c->adj_seg = nullptr, c->adj_bytes -= c->adj_seg_cap * state;
         c->adj_seg_cap = 0;
         if ((st = grow(reinterpret_cast<void**>(&c->adj_seg), seg * state))) return st;
@@ -1472,6 +1491,43 @@ extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* 
     return CMRT_OK;
 }
 
+// The graph of one checkpoint segment of `len` steps whose reverse sweep
+// starts from adjoint buffer `a`: recompute the states 1 .. len - 1 of the
+// segment buffer from slot 0 (the checkpoint), then the reverse steps
+// len - 1 .. 0.  Recorded on the first use of (len, a) -- on a private
+// stream, so the caller's stream may be any -- and replayed afterwards.
+cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out) {
+    for (const Ctx::AdjGraph& g : c->adj_graphs)
+        if (g.len == len && g.a == a) {
+            *out = g.exec;
+            return CMRT_OK;
+        }
+    if (!c->adj_capture) CK(c, cudaStreamCreateWithFlags(&c->adj_capture, cudaStreamNonBlocking));
+    const size_t n18 = 18 * cells(*c);
+    auto slot = [&](int64_t j) { return c->adj_seg + static_cast<size_t>(j) * n18; };
+    cudaStream_t user = c->stream;
+    c->stream = c->adj_capture;  // the launchers enqueue on c->stream
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->adj_capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int64_t j = 1; j < len && e == cudaSuccess; ++j) step_once(c, slot(j - 1), slot(j), &e);
+        int aa = a;
+        for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j, aa ^= 1)
+            e = cmrt::launch_adjoint_step(slot(j), c->adj_lam[aa], c->sp, c->adj_scratch, c->adj_partials,
+                                          c->adj_lam[aa ^ 1], c->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c->adj_capture, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    c->stream = user;
+    if (e != cudaSuccess) return fail(c, CMRT_ECUDA, "recording the adjoint segment graph failed: %s", cudaGetErrorString(e));
+    c->adj_graphs.push_back({len, a, exec});
+    *out = exec;
+    return CMRT_OK;
+}
+
 extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_every, const float* target, double* J,
                                     double grad_params[6], float* grad_rho_n0) {
     Ctx* c = live(h);
@@ -1485,8 +1541,8 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
     const int64_t K = ckpt_every;
     const size_t nck = static_cast<size_t>((nsteps + K - 1) / K);
-    const size_t seg = static_cast<size_t>(std::min<int64_t>(K, nsteps) - 1);
-    cmrt_status st = ensure_adj(c, nck, seg > 0 ? seg : 1);
+    const size_t seg = static_cast<size_t>(std::min<int64_t>(K, nsteps));
+    cmrt_status st = ensure_adj(c, nck, seg);
     if (st != CMRT_OK) return st;
     const size_t n = cells(*c), n18 = 18 * n;
     const size_t state = n18 * sizeof(float);
@@ -1512,20 +1568,19 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     CK(c, cmrt::launch_adjoint_seed(static_cast<const float*>(c->buf[c->cur]), d_target, c->sp, c->adj_scratch,
                                     c->adj_partials, c->adj_lam[a], c->stream));
     c->launches += 2;
-    // segments in reverse: recompute the states from the checkpoint, then reverse them
+    // segments in reverse: the checkpoint goes to slot 0 of the segment
+    // buffer, then one graph recomputes the segment's states from it and runs
+    // its reverse steps
+    const int per_step = c->p.stencil_order == 6 ? 4 : 1;
     for (int64_t k = static_cast<int64_t>(nck) - 1; k >= 0; --k) {
-        const int64_t s0 = k * K, s1 = std::min(s0 + K, nsteps);
-        const float* ck = c->adj_ckpt + static_cast<size_t>(k) * n18;
-        auto state_of = [&](int64_t j) { return j == 0 ? ck : c->adj_seg + static_cast<size_t>(j - 1) * n18; };
-        for (int64_t j = 1; j < s1 - s0; ++j) {
-            STEP(c, state_of(j - 1), c->adj_seg + static_cast<size_t>(j - 1) * n18);
-        }
-        for (int64_t t = s1 - 1; t >= s0; --t) {
-            CK(c, cmrt::launch_adjoint_step(state_of(t - s0), c->adj_lam[a], c->sp, c->adj_scratch, c->adj_partials,
-                                            c->adj_lam[a ^ 1], c->stream));
-            c->launches += cmrt::adj_launches_per_step(c->sp);
-            a ^= 1;
-        }
+        const int64_t len = std::min((k + 1) * K, nsteps) - k * K;
+        CK(c, cudaMemcpyAsync(c->adj_seg, c->adj_ckpt + static_cast<size_t>(k) * n18, state, cudaMemcpyDeviceToDevice,
+                              c->stream));
+        cudaGraphExec_t exec = nullptr;
+        if ((st = adj_segment_graph(c, len, a, &exec)) != CMRT_OK) return st;
+        CK(c, cudaGraphLaunch(exec, c->stream));
+        c->launches += (len - 1) * per_step + len * cmrt::adj_launches_per_step(c->sp);
+        a ^= static_cast<int>(len & 1);
     }
     if (grad_rho_n0) {
         // f(0) and dJ/df(0): the gather of P_{-1} and of its adjoint (a permutation)

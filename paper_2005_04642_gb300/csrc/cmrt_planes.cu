@@ -34,9 +34,11 @@
 // the terms of the row's own nodes with the ghost's parity.
 //
 // Parameter gradients (sigma, beta, lambda3_r, lambda3_b, g_acc) are reduced
-// per CTA in FP64 and accumulated across steps in a per-CTA FP64 slot (no
-// atomics: every launch of a pass uses the same grid, and the slots are
-// summed once at the end).
+// per CTA (FP32 within a warp, FP64 from there) and accumulated across steps
+// in a per-CTA FP64 slot (no atomics: every launch of a pass uses the same
+// grid, and the slots are summed once at the end).
+#include <type_traits>
+
 #include "cmrt_device.cuh"
 
 namespace cmrt {
@@ -53,36 +55,74 @@ enum Plane : int {
 };
 static_assert(kNumPlanes == kAdjPlanes, "scratch plane count");
 
-struct Lat {
-    int nx, ny, walls;
-    size_t n;
-    __device__ __forceinline__ size_t at(int x, int y) const { return static_cast<size_t>(y) * nx + x; }
-    __device__ __forceinline__ int wx(int x) const {
-        int r = x % nx;
-        return r < 0 ? r + nx : r;
+// periodic image of v in [0, n); the integer modulo only for images more than
+// one period away (lattices narrower than a stencil's reach)
+__device__ __forceinline__ int wrap_to(int v, int n) {
+    if (v >= 0 && v < n) return v;
+    if (v < 0 && v + n >= 0) return v + n;
+    if (v >= n && v - n < n) return v - n;
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// App. B coefficients a_N of the order-6 stencil
+__host__ __device__ constexpr float order6_coef(int N) { return N == 1 ? 4.5f : (N == 2 ? -0.9f : 0.1f); }
+
+// Neighbourhood of node (x, y) out to distance R in the planes: the periodic
+// images of the columns x - R .. x + R and the offsets of the rows y - R ..
+// y + R -- periodic images, or with walls W the mirror rows -1 - y' below
+// y = -1/2 and 2 ny - 1 - y' above y = ny - 1/2, flagged because odd fields
+// change sign there.  Computed once per thread, so every stencil read is a
+// plain indexed load; a CTA covers part of one row, so the row offsets and
+// the wall branches are uniform across it.
+template <int R, bool W>
+struct Nbh {
+    int nx, ny, x, y;
+    size_t n, o;  // plane size; this node
+    int col[2 * R + 1];
+    size_t row[2 * R + 1];
+    bool mir[2 * R + 1];
+
+    __device__ __forceinline__ Nbh(const StepParams& P, int x_, int y_) : nx(P.nx), ny(P.ny), x(x_), y(y_) {
+        n = static_cast<size_t>(nx) * ny;
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            col[d + R] = wrap_to(x + d, nx);
+            int yy = y + d;
+            bool m = false;
+            if (W) {
+                if (yy < 0) {
+                    yy = -1 - yy;
+                    m = true;
+                } else if (yy >= ny) {
+                    yy = 2 * ny - 1 - yy;
+                    m = true;
+                }
+            } else {
+                yy = wrap_to(yy, ny);
+            }
+            row[d + R] = static_cast<size_t>(yy) * nx;
+            mir[d + R] = m;
+        }
+        o = row[R] + x;
     }
-    __device__ __forceinline__ int wy(int y) const {
-        int r = y % ny;
-        return r < 0 ? r + ny : r;
+
+    // value of a plane at (x + dx, y + dy); `parity` multiplies a mirrored value
+    __device__ __forceinline__ float val(const float* a, int dx, int dy, float parity) const {
+        const float v = a[row[dy + R] + col[dx + R]];
+        return (W && mir[dy + R]) ? parity * v : v;
     }
-    // value of a plane at (x, y) (x periodic; y periodic, or mirrored across
-    // the wall planes with the given parity)
-    __device__ __forceinline__ float val(const float* a, int x, int y, float parity) const {
-        x = wx(x);
-        if (!walls) return a[at(x, wy(y))];
-        if (y < 0) return parity * a[at(x, -1 - y)];
-        if (y >= ny) return parity * a[at(x, 2 * ny - 1 - y)];
-        return a[at(x, y)];
-    }
-    // gradient of a plane at (x, y): the compact stencil (Sec. 2) for ORDER 2,
-    // App. B's radius-3 stencil for ORDER 6
+
+    // gradient of a plane at this node: the compact stencil (Sec. 2) for
+    // ORDER 2, App. B's radius-3 stencil for ORDER 6
     template <int ORDER>
-    __device__ __forceinline__ void grad(const float* a, int x, int y, float parity, float& gx, float& gy) const {
+    __device__ __forceinline__ void grad(const float* a, float parity, float& gx, float& gy) const {
+        static_assert(R >= (ORDER == 6 ? 3 : 1), "neighbourhood too small for the stencil");
         if (ORDER == 2) {
-            const float e = val(a, x + 1, y, parity), w = val(a, x - 1, y, parity);
-            const float n_ = val(a, x, y + 1, parity), s = val(a, x, y - 1, parity);
-            const float ne = val(a, x + 1, y + 1, parity), nw = val(a, x - 1, y + 1, parity);
-            const float se = val(a, x + 1, y - 1, parity), sw = val(a, x - 1, y - 1, parity);
+            const float e = val(a, 1, 0, parity), w = val(a, -1, 0, parity);
+            const float n_ = val(a, 0, 1, parity), s = val(a, 0, -1, parity);
+            const float ne = val(a, 1, 1, parity), nw = val(a, -1, 1, parity);
+            const float se = val(a, 1, -1, parity), sw = val(a, -1, -1, parity);
             gx = ddx(e, w, ne, nw, se, sw);
             gy = ddy(n_, s, ne, nw, se, sw);
         } else {
@@ -92,19 +132,21 @@ struct Lat {
             for (int N = 1; N <= 3; ++N) {
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
-                    const float v = val(a, x + N * lcx(i), y + N * lcy(i), parity);
+                    const float v = val(a, N * lcx(i), N * lcy(i), parity);
                     if (lcx(i)) gx = fmaf(order6_coef(N) * lw(i) * float(lcx(i)), v, gx);
                     if (lcy(i)) gy = fmaf(order6_coef(N) * lw(i) * float(lcy(i)), v, gy);
                 }
             }
         }
     }
+
     // transpose of one component (XC: x, else y) of grad<ORDER>, applied to
     // a plane: sum over the stencil's reach N c_i of k a(r - N c_i) for nodes
     // of the lattice, plus, next to a wall, the nodes whose stencil read this
     // node as a mirrored ghost (mirror row -1 - y' below, 2 ny - 1 - y' above)
     template <bool XC, int ORDER>
-    __device__ __forceinline__ float gradT(const float* a, int x, int y, float parity) const {
+    __device__ __forceinline__ float gradT(const float* a, float parity) const {
+        static_assert(R >= (ORDER == 6 ? 3 : 1), "neighbourhood too small for the stencil");
         float acc = 0.0f;
 #pragma unroll
         for (int N = 1; N <= (ORDER == 6 ? 3 : 1); ++N) {
@@ -113,49 +155,53 @@ struct Lat {
                 const int c = XC ? lcx(i) : lcy(i);
                 if (c == 0) continue;
                 const float k = (ORDER == 6 ? order6_coef(N) : 3.0f) * lw(i) * float(c);
-                const int xs = wx(x - N * lcx(i));
-                const int dy = N * lcy(i);
-                const int ys = y - dy;
-                if (!walls) {
-                    acc = fmaf(k, a[at(xs, wy(ys))], acc);
+                const int dx = -N * lcx(i), dy = -N * lcy(i);  // the node r - N c_i
+                if (!W) {
+                    acc = fmaf(k, a[row[dy + R] + col[dx + R]], acc);
                 } else {
-                    if (ys >= 0 && ys < ny) acc = fmaf(k, a[at(xs, ys)], acc);
-                    const int yb = -1 - y - dy;  // node whose read below y = -1/2 mirrors onto row y
-                    if (yb >= 0 && yb < ny && yb + dy < 0) acc = fmaf(parity * k, a[at(xs, yb)], acc);
-                    const int yt = 2 * ny - 1 - y - dy;  // same above y = ny - 1/2
-                    if (yt >= 0 && yt < ny && yt + dy >= ny) acc = fmaf(parity * k, a[at(xs, yt)], acc);
+                    if (!mir[dy + R]) acc = fmaf(k, a[row[dy + R] + col[dx + R]], acc);
+                    const int yb = -1 - y + dy;  // node whose read below y = -1/2 mirrors onto row y
+                    if (yb >= 0 && yb < ny && yb - dy < 0)
+                        acc = fmaf(parity * k, a[static_cast<size_t>(yb) * nx + col[dx + R]], acc);
+                    const int yt = 2 * ny - 1 - y + dy;  // same above y = ny - 1/2
+                    if (yt >= 0 && yt < ny && yt - dy >= ny)
+                        acc = fmaf(parity * k, a[static_cast<size_t>(yt) * nx + col[dx + R]], acc);
                 }
             }
         }
         return acc;
     }
-    // App. B coefficients a_N of the order-6 stencil
-    __host__ __device__ static constexpr float order6_coef(int N) { return N == 1 ? 4.5f : (N == 2 ? -0.9f : 0.1f); }
+
+    // pre-collision populations of this node: f_i(r) = P_i(r - c_i), or
+    // P_opp(i)(r) where r - c_i lies beyond a wall (half-way bounce-back)
+    __device__ __forceinline__ void gather(const float* __restrict__ post, float (&fr)[9], float (&fb)[9]) const {
+        static_assert(R >= 1, "the gather reads the nearest neighbours");
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            size_t src;
+            int li = i;
+            if (W && mir[-lcy(i) + R]) {
+                li = lopp(i);
+                src = o;
+            } else {
+                src = row[-lcy(i) + R] + col[-lcx(i) + R];
+            }
+            fr[i] = post[static_cast<size_t>(li) * n + src];
+            fb[i] = post[static_cast<size_t>(9 + li) * n + src];
+        }
+    }
 };
 
-__device__ __forceinline__ Lat lattice(const StepParams& P) {
-    return Lat{P.nx, P.ny, P.wall_y, static_cast<size_t>(P.nx) * P.ny};
-}
+// the neighbourhood a stencil of the given order needs
+template <int ORDER>
+constexpr int reach() { return ORDER == 6 ? 3 : 1; }
 
-// pre-collision populations of node (x, y): f_i(r) = P_i(r - c_i), or
-// P_opp(i)(r) where r - c_i lies beyond a wall (half-way bounce-back)
-__device__ __forceinline__ void gather_node(const float* __restrict__ post, const Lat& L, int x, int y,
-                                            float (&fr)[9], float (&fb)[9]) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int sy = y - lcy(i);
-        size_t o;
-        int li = i;
-        if (L.walls && (sy < 0 || sy >= L.ny)) {
-            li = lopp(i);
-            o = L.at(x, y);
-        } else {
-            o = L.at(L.wx(x - lcx(i)), L.wy(sy));
-        }
-        fr[i] = post[static_cast<size_t>(li) * L.n + o];
-        fb[i] = post[static_cast<size_t>(9 + li) * L.n + o];
-    }
-}
+// a node's own offset in the planes (per-node passes without a stencil)
+struct Own {
+    size_t n, o;
+    __device__ __forceinline__ Own(const StepParams& P, int x, int y)
+        : n(static_cast<size_t>(P.nx) * P.ny), o(static_cast<size_t>(y) * P.nx + x) {}
+};
 
 __device__ __forceinline__ float sum9f(const float (&v)[9]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
@@ -176,9 +222,12 @@ __device__ __forceinline__ void normalise_T(float gx, float gy, float bx, float 
     }
 }
 
-// FP64 CTA reduction of up to 7 values, added into this CTA's slot.
+// CTA reduction of up to 7 per-node terms, added into this CTA's FP64 slot:
+// FP32 products and warp sums of 32 terms (GB300's FP64 rate is a small
+// fraction of its FP32 rate), FP64 from the warp partials on -- across the
+// CTA's warps and, in the slot, across all steps of the adjoint sweep.
 template <int N>
-__device__ __forceinline__ void add_partials(double (&v)[N], const int* slots, double* __restrict__ partials) {
+__device__ __forceinline__ void add_partials(float (&v)[N], const int* slots, double* __restrict__ partials) {
     __shared__ double red[kAT / 32][N];
 #pragma unroll
     for (int j = 0; j < N; ++j)
@@ -198,18 +247,19 @@ __device__ __forceinline__ void add_partials(double (&v)[N], const int* slots, d
 }
 
 // ----------------------------------------------------------------- forward recomputation
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_fwd_moments(const float* __restrict__ post, const StepParams P,
                                                       float* __restrict__ S) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
+    if (x >= P.nx) return;
+    const Nbh<1, W> L(P, x, y);
     float fr[9], fb[9];
-    gather_node(post, L, x, y, fr, fb);
+    L.gather(post, fr, fb);
     const float rr = sum9f(fr), rb = sum9f(fb);
     float f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
-    const size_t o = L.at(x, y);
+    const size_t o = L.o;
     S[kRR * L.n + o] = rr;
     S[kRB * L.n + o] = rb;
     S[kJX * L.n + o] = ((f[1] + f[7]) + f[8]) - ((f[3] + f[5]) + f[4]);
@@ -224,20 +274,18 @@ __global__ void __launch_bounds__(kAT) k_fwd_moments(const float* __restrict__ p
     S[kPHIP * L.n + o] = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
 }
 
+template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_fwd_normal(const StepParams P, float* __restrict__ S) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
+    if (x >= P.nx) return;
+    const Nbh<reach<ORDER>(), W> L(P, x, y);
     // grad rho^N = 2 grad chi_R = -2 grad chi_B (the stencil weights sum to
     // zero): the same stencil, evaluated on the fraction that is small here
-    const size_t o = L.at(x, y);
+    const size_t o = L.o;
     float gx, gy;
     const bool red_minor = S[kCHR * L.n + o] < S[kCHB * L.n + o];
     const float* ch = S + (red_minor ? kCHR : kCHB) * L.n;
-    if (P.stencil_order == 6)
-        L.grad<6>(ch, x, y, 1.0f, gx, gy);
-    else
-        L.grad<2>(ch, x, y, 1.0f, gx, gy);
+    L.template grad<ORDER>(ch, 1.0f, gx, gy);
     gx *= red_minor ? 2.0f : -2.0f;
     gy *= red_minor ? 2.0f : -2.0f;
     S[kGX * L.n + o] = gx;
@@ -251,26 +299,24 @@ __device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& 
     ny = -gy * inv;
 }
 
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_fwd_force(const StepParams P, float* __restrict__ S) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
+    if (x >= P.nx) return;
+    const Nbh<1, W> L(P, x, y);
     float K = P.fixed_K;
     if (P.curvature_mode == 0) {
         // K = div n-hat with n-hat of the neighbours (x even, y odd beyond a wall)
         float nxv[9], nyv[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const int yy = y + lcy(i);
-            const bool ghost = L.walls && (yy < 0 || yy >= L.ny);
-            const int ys = !L.walls ? L.wy(yy) : (yy < 0 ? -1 - yy : (yy >= L.ny ? 2 * L.ny - 1 - yy : yy));
-            const size_t o = L.at(L.wx(x + lcx(i)), ys);
+            const size_t o = L.row[lcy(i) + 1] + L.col[lcx(i) + 1];
             normal_of(S[kGX * L.n + o], S[kGY * L.n + o], nxv[i], nyv[i]);
-            if (ghost) nyv[i] = -nyv[i];
+            if (W && L.mir[lcy(i) + 1]) nyv[i] = -nyv[i];
         }
         K = ddx(nxv[8], nxv[4], nxv[1], nxv[3], nxv[7], nxv[5]) + ddy(nyv[2], nyv[6], nyv[1], nyv[3], nyv[7], nyv[5]);
     }
-    const size_t o = L.at(x, y);
+    const size_t o = L.o;
     const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
     const float rho = S[kRR * L.n + o] + S[kRB * L.n + o];
     const float hk = P.half_sigma * K;
@@ -286,16 +332,17 @@ __global__ void __launch_bounds__(kAT) k_fwd_force(const StepParams P, float* __
 // ----------------------------------------------------------------- reverse passes
 // Reverse of the per-node collision and recolour (App. A Eqs. 38, eq84;
 // Eq. eq_re_color).  lam: adjoint of the post-collision state P_t (18 planes).
+template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ post, const float* __restrict__ lam,
                                                       const StepParams P, float* __restrict__ S,
                                                       double* __restrict__ partials) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    double acc[3] = {0.0, 0.0, 0.0};  // beta, lambda3_r, lambda3_b
-    if (x < L.nx) {
-        const size_t o = L.at(x, y);
+    float acc[3] = {0.0f, 0.0f, 0.0f};  // beta, lambda3_r, lambda3_b
+    if (x < P.nx) {
+        const Nbh<reach<ORDER>(), W> L(P, x, y);
+        const size_t o = L.o;
         float fr[9], fb[9], f[9];
-        gather_node(post, L, x, y, fr, fb);
+        L.gather(post, fr, fb);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
         const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
@@ -305,12 +352,9 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
         const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
         const float rn = S[kCHR * L.n + o] - S[kCHB * L.n + o];
         float dPx, dPy, dux, duy, t0, t1;
-        if (P.stencil_order == 6)
-            L.grad<6>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
-        else
-            L.grad<2>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
-        L.grad<2>(S + kUX * L.n, x, y, -1.0f, dux, t0);
-        L.grad<2>(S + kUY * L.n, x, y, -1.0f, t1, duy);
+        L.template grad<ORDER>(S + kPHIP * L.n, 1.0f, dPx, dPy);
+        L.template grad<2>(S + kUX * L.n, -1.0f, dux, t0);
+        L.template grad<2>(S + kUY * L.n, -1.0f, t1, duy);
         const float divu = dux + duy;
         // ---- forward values at this node
         float nu, dnu_drn = 0.0f;
@@ -382,7 +426,7 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
                 eyb = fmaf(db * seg * lw(i) * phim, chy(i), eyb);
             }
         }
-        acc[0] = static_cast<double>(segb) * (rr * rb * ir);
+        acc[0] = segb * (rr * rb * ir);
         float rrb = (xRb - xBb) * rb * ir2;
         float rbb = (xBb - xRb) * rr * ir2;
         rrb = fmaf(segb * P.beta, rb * rb * ir2, rrb);
@@ -457,8 +501,8 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
             rnb = nub * dnu_drn;
             // nu_C = (2 / lambda3_C - 1) / 6: d nu_C / d lambda3_C = -(6 nu_C + 1)^2 / 12
             const float dr = fmaf(6.0f, P.nu_r, 1.0f), db = fmaf(6.0f, P.nu_b, 1.0f);
-            acc[1] = static_cast<double>(nub * 0.5f * (1.0f + rn)) * (-(double)dr * dr / 12.0);
-            acc[2] = static_cast<double>(nub * 0.5f * (1.0f - rn)) * (-(double)db * db / 12.0);
+            acc[1] = nub * 0.5f * (1.0f + rn) * (-dr * dr * (1.0f / 12.0f));
+            acc[2] = nub * 0.5f * (1.0f - rn) * (-db * db * (1.0f / 12.0f));
         } else {
             rhob = fmaf(nub, -P.eta * ir2, rhob);
         }
@@ -480,15 +524,16 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
 }
 
 // Reverse of div u, u = (j + G/2) / rho and G = sigma K g / 2 + rho g_acc + g_vol.
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_rev_force(const StepParams P, float* __restrict__ S,
                                                     double* __restrict__ partials) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    double acc[3] = {0.0, 0.0, 0.0};  // sigma, g_acc_x, g_acc_y
-    if (x < L.nx) {
-        const size_t o = L.at(x, y);
-        const float uxt = S[kUXB * L.n + o] + L.gradT<true, 2>(S + kDIVUB * L.n, x, y, -1.0f);
-        const float uyt = S[kUYB * L.n + o] + L.gradT<false, 2>(S + kDIVUB * L.n, x, y, -1.0f);
+    float acc[3] = {0.0f, 0.0f, 0.0f};  // sigma, g_acc_x, g_acc_y
+    if (x < P.nx) {
+        const Nbh<1, W> L(P, x, y);
+        const size_t o = L.o;
+        const float uxt = S[kUXB * L.n + o] + L.template gradT<true, 2>(S + kDIVUB * L.n, -1.0f);
+        const float uyt = S[kUYB * L.n + o] + L.template gradT<false, 2>(S + kDIVUB * L.n, -1.0f);
         const float rho = S[kRR * L.n + o] + S[kRB * L.n + o];
         const float ir = 1.0f / rho;
         const float ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
@@ -504,22 +549,23 @@ __global__ void __launch_bounds__(kAT) k_rev_force(const StepParams P, float* __
         S[kGYB * L.n + o] += P.half_sigma * K * Gyt;
         S[kRRB * L.n + o] += rhob;
         S[kRBB * L.n + o] += rhob;
-        acc[0] = 0.5 * static_cast<double>(K) * gG;
-        acc[1] = static_cast<double>(rho) * Gxt;
-        acc[2] = static_cast<double>(rho) * Gyt;
+        acc[0] = 0.5f * K * gG;
+        acc[1] = rho * Gxt;
+        acc[2] = rho * Gyt;
     }
     const int slots[3] = {0, 4, 5};
     add_partials<3>(acc, slots, partials);
 }
 
 // Reverse of K = d_x n_x + d_y n_y and n-hat = -g / max(|g|, eps).
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_rev_normal(const StepParams P, float* __restrict__ S) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
-    const float nxb = L.gradT<true, 2>(S + kKB * L.n, x, y, 1.0f);
-    const float nyb = L.gradT<false, 2>(S + kKB * L.n, x, y, -1.0f);
+    if (x >= P.nx) return;
+    const Nbh<1, W> L(P, x, y);
+    const size_t o = L.o;
+    const float nxb = L.template gradT<true, 2>(S + kKB * L.n, 1.0f);
+    const float nyb = L.template gradT<false, 2>(S + kKB * L.n, -1.0f);
     float tx, ty;
     normalise_T(S[kGX * L.n + o], S[kGY * L.n + o], nxb, nyb, tx, ty);
     S[kGXB * L.n + o] -= tx;
@@ -528,19 +574,16 @@ __global__ void __launch_bounds__(kAT) k_rev_normal(const StepParams P, float* _
 
 // Reverse of grad rho^N, grad Phi', rho^N, Phi' and of the moments: leaves
 // the population adjoint dJ/dC_i(r, t) = FB_i + (c_i . j-bar) + rho_C-bar.
+template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_rev_moments(const StepParams P, float* __restrict__ S) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
-    float rnb = S[kRNB * L.n + o], phb;
-    if (P.stencil_order == 6) {
-        rnb += L.gradT<true, 6>(S + kGXB * L.n, x, y, 1.0f) + L.gradT<false, 6>(S + kGYB * L.n, x, y, 1.0f);
-        phb = L.gradT<true, 6>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false, 6>(S + kDPYB * L.n, x, y, 1.0f);
-    } else {
-        rnb += L.gradT<true, 2>(S + kGXB * L.n, x, y, 1.0f) + L.gradT<false, 2>(S + kGYB * L.n, x, y, 1.0f);
-        phb = L.gradT<true, 2>(S + kDPXB * L.n, x, y, 1.0f) + L.gradT<false, 2>(S + kDPYB * L.n, x, y, 1.0f);
-    }
+    if (x >= P.nx) return;
+    const Nbh<reach<ORDER>(), W> L(P, x, y);
+    const size_t o = L.o;
+    float rnb = S[kRNB * L.n + o];
+    rnb += L.template gradT<true, ORDER>(S + kGXB * L.n, 1.0f) + L.template gradT<false, ORDER>(S + kGYB * L.n, 1.0f);
+    const float phb =
+        L.template gradT<true, ORDER>(S + kDPXB * L.n, 1.0f) + L.template gradT<false, ORDER>(S + kDPYB * L.n, 1.0f);
     const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
     const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
     const float iden = 1.0f / ((a + b) * (a + b));
@@ -558,22 +601,22 @@ __global__ void __launch_bounds__(kAT) k_rev_moments(const StepParams P, float* 
 
 // Transpose of the streaming gather: lam_i(s) = fbar_i(s + c_i), or
 // fbar_opp(i)(s) where s + c_i lies beyond a wall.
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_rev_gather(const StepParams P, const float* __restrict__ S,
                                                      float* __restrict__ lam_out) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
+    if (x >= P.nx) return;
+    const Nbh<1, W> L(P, x, y);
+    const size_t o = L.o;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const int ty = y + lcy(i);
         size_t src;
         int li = i;
-        if (L.walls && (ty < 0 || ty >= L.ny)) {
+        if (W && L.mir[lcy(i) + 1]) {
             li = lopp(i);
             src = o;
         } else {
-            src = L.at(L.wx(x + lcx(i)), L.wy(ty));
+            src = L.row[lcy(i) + 1] + L.col[lcx(i) + 1];
         }
         const float common = S[static_cast<size_t>(kFB0 + li) * L.n + src];
         lam_out[static_cast<size_t>(i) * L.n + o] = common + S[kRRB * L.n + src];
@@ -584,10 +627,10 @@ __global__ void __launch_bounds__(kAT) k_rev_gather(const StepParams P, const fl
 // dJ/df(t) in the public pre-collision layout: fbar_i + rho_C-bar at the node.
 __global__ void __launch_bounds__(kAT) k_rev_expand(const StepParams P, const float* __restrict__ S,
                                                      float* __restrict__ lam_pre) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
+    if (x >= P.nx) return;
+    const Own L(P, x, y);
+    const size_t o = L.o;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float common = S[static_cast<size_t>(kFB0 + i) * L.n + o];
@@ -598,20 +641,21 @@ __global__ void __launch_bounds__(kAT) k_rev_expand(const StepParams P, const fl
 
 // Objective J = 1/2 sum (rho^N - target)^2 of f(T) = gather(P_{T-1}) and its
 // gradient dJ/dC_i = (rho^N - target) d rho^N / d rho_C, the same for every link.
+template <bool W>
 __global__ void __launch_bounds__(kAT) k_seed(const float* __restrict__ post, const float* __restrict__ target,
                                                const StepParams P, float* __restrict__ S,
                                                double* __restrict__ partials) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    double acc[1] = {0.0};
-    if (x < L.nx) {
-        const size_t o = L.at(x, y);
+    float acc[1] = {0.0f};
+    if (x < P.nx) {
+        const Nbh<1, W> L(P, x, y);
+        const size_t o = L.o;
         float fr[9], fb[9];
-        gather_node(post, L, x, y, fr, fb);
+        L.gather(post, fr, fb);
         const float a = sum9f(fr) * P.inv_rho0_r, b = sum9f(fb) * P.inv_rho0_b;
         const float res = (a - b) / (a + b) - target[o];
         const float iden = 1.0f / ((a + b) * (a + b));
-        acc[0] = 0.5 * static_cast<double>(res) * res;
+        acc[0] = 0.5f * res * res;
         S[kRRB * L.n + o] = res * 2.0f * b * iden * P.inv_rho0_r;
         S[kRBB * L.n + o] = res * -2.0f * a * iden * P.inv_rho0_b;
 #pragma unroll
@@ -626,10 +670,10 @@ __global__ void __launch_bounds__(kAT) k_seed(const float* __restrict__ post, co
 // state (pre-collision, public layout), lam0 its adjoint.
 __global__ void __launch_bounds__(kAT) k_init_T(const float* __restrict__ pre0, const float* __restrict__ lam0,
                                                  const StepParams P, float* __restrict__ grad) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
+    if (x >= P.nx) return;
+    const Own L(P, x, y);
+    const size_t o = L.o;
     float R[9], B[9], f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -667,27 +711,25 @@ __global__ void __launch_bounds__(kAT) k_init_T(const float* __restrict__ pre0, 
 // ----------------------------------------------------------------- order-6 step and its outputs
 // The rest of one step after k_fwd_*: grad Phi' (order of P.stencil_order),
 // div u, collision in moment space, recolour and store of P_t (FP32 layout).
+template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_step_planes(const float* __restrict__ post, float* __restrict__ dst,
                                                       const StepParams P, const float* __restrict__ S,
                                                       unsigned* __restrict__ flag) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
+    if (x >= P.nx) return;
+    const Nbh<reach<ORDER>(), W> L(P, x, y);
+    const size_t o = L.o;
     float fr[9], fb[9], f[9];
-    gather_node(post, L, x, y, fr, fb);
+    L.gather(post, fr, fb);
     const float rr = sum9f(fr), rb = sum9f(fb);
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
     const float rho = rr + rb;
     if (!isfinite(rho)) atomicOr(flag, 1u);
     float dPx, dPy, dux, duy, t0, t1;
-    if (P.stencil_order == 6)
-        L.grad<6>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
-    else
-        L.grad<2>(S + kPHIP * L.n, x, y, 1.0f, dPx, dPy);
-    L.grad<2>(S + kUX * L.n, x, y, -1.0f, dux, t0);
-    L.grad<2>(S + kUY * L.n, x, y, -1.0f, t1, duy);
+    L.template grad<ORDER>(S + kPHIP * L.n, 1.0f, dPx, dPy);
+    L.template grad<2>(S + kUX * L.n, -1.0f, dux, t0);
+    L.template grad<2>(S + kUY * L.n, -1.0f, t1, duy);
     const float inv_rho = rcp(rho);
     float nu;
     if (P.visc_mode == 0) {
@@ -710,10 +752,10 @@ __global__ void __launch_bounds__(kAT) k_step_planes(const float* __restrict__ p
 
 __global__ void __launch_bounds__(kAT) k_fields_planes(const StepParams P, const float* __restrict__ S,
                                                         FieldOut fo) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
-    if (x >= L.nx) return;
-    const size_t o = L.at(x, y);
+    if (x >= P.nx) return;
+    const Own L(P, x, y);
+    const size_t o = L.o;
     const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
     if (fo.rho_r) fo.rho_r[o] = rr;
     if (fo.rho_b) fo.rho_b[o] = rb;
@@ -725,11 +767,11 @@ __global__ void __launch_bounds__(kAT) k_fields_planes(const StepParams P, const
 // FP64 per-CTA partial diagnostics, partials[block][kDiagSlots] (slot 4 is a maximum)
 __global__ void __launch_bounds__(kAT) k_diag_planes(const StepParams P, const float* __restrict__ S,
                                                       double* __restrict__ partials) {
-    const Lat L = lattice(P);
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
     double v[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (x < L.nx) {
-        const size_t o = L.at(x, y);
+    if (x < P.nx) {
+        const Own L(P, x, y);
+        const size_t o = L.o;
         const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
         if (isfinite(rr + rb)) {
             const double ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
@@ -789,24 +831,39 @@ __global__ void k_adj_reduce(const double* __restrict__ partials, int nblocks, d
 
 dim3 adj_grid(const StepParams& P) { return dim3(static_cast<unsigned>((P.nx + kAT - 1) / kAT), P.ny, 1); }
 
+// Calls f(order, walls) with both as compile-time constants.
+template <class F>
+void dispatch(const StepParams& P, F&& f) {
+    using O2 = std::integral_constant<int, 2>;
+    using O6 = std::integral_constant<int, 6>;
+    if (P.stencil_order == 6) {
+        if (P.wall_y) f(O6{}, std::true_type{});
+        else f(O6{}, std::false_type{});
+    } else {
+        if (P.wall_y) f(O2{}, std::true_type{});
+        else f(O2{}, std::false_type{});
+    }
+}
+
 // moments, colour fractions, Phi', grad rho^N, K, G and u of P_{t-1} into the planes
+template <int O, bool W>
 void forward_planes(const float* post, const StepParams& P, float* S, cudaStream_t s) {
     const dim3 g = adj_grid(P);
-    k_fwd_moments<<<g, kAT, 0, s>>>(post, P, S);
-    k_fwd_normal<<<g, kAT, 0, s>>>(P, S);
-    k_fwd_force<<<g, kAT, 0, s>>>(P, S);
+    k_fwd_moments<W><<<g, kAT, 0, s>>>(post, P, S);
+    k_fwd_normal<O, W><<<g, kAT, 0, s>>>(P, S);
+    k_fwd_force<W><<<g, kAT, 0, s>>>(P, S);
 }
 
 // the reverse passes shared by both forms of one adjoint step
-cudaError_t reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
-                         cudaStream_t s) {
+template <int O, bool W>
+void reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
+                  cudaStream_t s) {
     const dim3 g = adj_grid(P);
-    forward_planes(post, P, S, s);
-    k_rev_collide<<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
-    k_rev_force<<<g, kAT, 0, s>>>(P, S, partials);
-    if (P.curvature_mode == 0) k_rev_normal<<<g, kAT, 0, s>>>(P, S);
-    k_rev_moments<<<g, kAT, 0, s>>>(P, S);
-    return cudaGetLastError();
+    forward_planes<O, W>(post, P, S, s);
+    k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
+    k_rev_force<W><<<g, kAT, 0, s>>>(P, S, partials);
+    if (P.curvature_mode == 0) k_rev_normal<W><<<g, kAT, 0, s>>>(P, S);
+    k_rev_moments<O, W><<<g, kAT, 0, s>>>(P, S);
 }
 
 }  // namespace
@@ -815,21 +872,23 @@ int adj_blocks(int nx, int ny) { return ((nx + kAT - 1) / kAT) * ny; }
 
 cudaError_t launch_step_planes(const float* post, float* dst, const StepParams& P, float* scratch, unsigned* flag,
                                cudaStream_t s) {
-    forward_planes(post, P, scratch, s);
-    k_step_planes<<<adj_grid(P), kAT, 0, s>>>(post, dst, P, scratch, flag);
+    dispatch(P, [&](auto o, auto w) {
+        forward_planes<decltype(o)::value, decltype(w)::value>(post, P, scratch, s);
+        k_step_planes<decltype(o)::value, decltype(w)::value><<<adj_grid(P), kAT, 0, s>>>(post, dst, P, scratch, flag);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_fields_planes(const float* post, const StepParams& P, float* scratch, FieldOut out,
                                  cudaStream_t s) {
-    forward_planes(post, P, scratch, s);
+    dispatch(P, [&](auto o, auto w) { forward_planes<decltype(o)::value, decltype(w)::value>(post, P, scratch, s); });
     k_fields_planes<<<adj_grid(P), kAT, 0, s>>>(P, scratch, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* scratch, double* partials,
                                cudaStream_t s) {
-    forward_planes(post, P, scratch, s);
+    dispatch(P, [&](auto o, auto w) { forward_planes<decltype(o)::value, decltype(w)::value>(post, P, scratch, s); });
     k_diag_planes<<<adj_grid(P), kAT, 0, s>>>(P, scratch, partials);
     return cudaGetLastError();
 }
@@ -838,16 +897,18 @@ int adj_launches_per_step(const StepParams& P) { return P.curvature_mode == 0 ? 
 
 cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                 double* partials, float* lam_prev, cudaStream_t s) {
-    cudaError_t e = reverse_core(post, lam_post, P, scratch, partials, s);
-    if (e != cudaSuccess) return e;
-    k_rev_gather<<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_prev);
+    dispatch(P, [&](auto o, auto w) {
+        reverse_core<decltype(o)::value, decltype(w)::value>(post, lam_post, P, scratch, partials, s);
+        k_rev_gather<decltype(w)::value><<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_prev);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                     double* partials, float* lam_pre, cudaStream_t s) {
-    cudaError_t e = reverse_core(post, lam_post, P, scratch, partials, s);
-    if (e != cudaSuccess) return e;
+    dispatch(P, [&](auto o, auto w) {
+        reverse_core<decltype(o)::value, decltype(w)::value>(post, lam_post, P, scratch, partials, s);
+    });
     k_rev_expand<<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_pre);
     return cudaGetLastError();
 }
@@ -855,8 +916,13 @@ cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, co
 cudaError_t launch_adjoint_seed(const float* post, const float* target, const StepParams& P, float* scratch,
                                 double* partials, float* lam_post, cudaStream_t s) {
     const dim3 g = adj_grid(P);
-    k_seed<<<g, kAT, 0, s>>>(post, target, P, scratch, partials);
-    k_rev_gather<<<g, kAT, 0, s>>>(P, scratch, lam_post);
+    if (P.wall_y) {
+        k_seed<true><<<g, kAT, 0, s>>>(post, target, P, scratch, partials);
+        k_rev_gather<true><<<g, kAT, 0, s>>>(P, scratch, lam_post);
+    } else {
+        k_seed<false><<<g, kAT, 0, s>>>(post, target, P, scratch, partials);
+        k_rev_gather<false><<<g, kAT, 0, s>>>(P, scratch, lam_post);
+    }
     return cudaGetLastError();
 }
 

@@ -167,6 +167,41 @@ def test_checkpoint_interval_gives_identical_gradients():
         assert np.array_equal(grn, outs[0][2])
 
 
+def test_recorded_segment_graphs_are_replayed_exactly():
+    """A second adjoint sweep on the same context replays the CUDA graphs
+    recorded by the first (same segment lengths and start buffers) and must
+    give the same objective and gradients bit for bit."""
+    nsteps = 12
+    d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4)
+    lat = cm.Lattice(d, rn0.astype(np.float32), None)
+    start = lat.populations().clone()
+    J1, g1, _ = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=5)
+    lat.set_populations(start)
+    J2, g2, _ = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=5)
+    lat.close()
+    assert J2 == J1
+    assert g2 == g1
+
+
+def test_checkpoint_interval_invariance_walls_order6():
+    """Walls and App. B's order-6 stencil inside the recorded segments (the
+    order-6 replay step is four launches): every checkpoint interval gives
+    the same gradients."""
+    nsteps = 7
+    d, rn0, u0, target = _drop_setup(24, 6.0, nsteps, g=1e-4, wall=True)
+    d["stencil_order"] = 6
+    outs = []
+    for K in (1, 3, 7):
+        lat = cm.Lattice(d, rn0.astype(np.float32), None)
+        J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=K, want_rho_n0=True)
+        outs.append((J, g, grn.cpu().numpy()))
+        lat.close()
+    for J, g, grn in outs[1:]:
+        assert J == outs[0][0]
+        assert g == outs[0][1]
+        assert np.array_equal(grn, outs[0][2])
+
+
 def test_adjoint_matches_finite_differences_64():
     """64^2 drop (radius 8), Lambda = 10, gravity 1e-5, 200 steps, checkpoints
     every 50: gradients with respect to sigma, beta, both shear rates, the
