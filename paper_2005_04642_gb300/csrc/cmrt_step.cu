@@ -45,11 +45,11 @@ namespace {
 constexpr int kPlanes = 18;
 // Rings of stage results, each holding only the rows its readers need (a
 // row is one float per window column; fields x and y interleaved by row):
-//   grad rho^N  2 rows  (written by B at row s - 2, read by C at row s - 3)
+//   grad rho^N  4 rows  (B writes row s - 2 while C may still read s - 4)
 //   n-hat       4 rows + the mirrored row ny beyond a wall
 //   G           4 rows  (C writes row s - 3 while D may still read s - 5)
 //   u           4 rows + the mirrored row ny
-constexpr int kBFloats = (2 * 2 + 5 * 2) * kWin;  // grad rho^N, n-hat
+constexpr int kBFloats = (4 * 2 + 5 * 2) * kWin;  // grad rho^N, n-hat
 constexpr int kCFloats = (4 * 2 + 5 * 2) * kWin;  // G, u
 
 // The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
@@ -63,6 +63,7 @@ constexpr int kStepThreads = 2 * kThreads;
 constexpr int kBarFront = 1;
 constexpr int kBarC = 2;  // 2, 3
 constexpr int kBarD = 4;  // 4, 5
+constexpr int kBarBack = 6;  // the back warps among themselves
 
 template <int ID, int N>
 __device__ __forceinline__ void bar_sync() {
@@ -354,8 +355,8 @@ struct Rings {
     __device__ __forceinline__ float* jx(int row) const { return a + ((row & 3) * 4 + 2) * kWin; }
     __device__ __forceinline__ float* jy(int row) const { return a + ((row & 3) * 4 + 3) * kWin; }
     __device__ __forceinline__ int slot4(int row) const { return (W && row == ghost) ? 4 : (row & 3); }
-    __device__ __forceinline__ float* grad(int row, int f) const { return b + ((row & 1) * 2 + f) * kWin; }
-    __device__ __forceinline__ float* nh(int row, int f) const { return b + (4 + slot4(row) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* grad(int row, int f) const { return b + ((row & 3) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* nh(int row, int f) const { return b + (8 + slot4(row) * 2 + f) * kWin; }
     __device__ __forceinline__ float* G(int row, int f) const { return c + ((row & 3) * 2 + f) * kWin; }
     __device__ __forceinline__ float* u(int row, int f) const { return c + (8 + slot4(row) * 2 + f) * kWin; }
 };
@@ -441,15 +442,16 @@ struct DiagAcc {
 // the ring slot of row s - 7.  The fields and diagnostics passes run all four
 // stages in every thread of a 128-thread CTA, one barrier between stages.
 // The step is warp-specialised (2 x 128 threads): the front threads wait for
-// the copies, issue the next one and run A, B and C of iteration k, then
-// publish them with bar.arrive; the back threads run D of iteration k while
-// the front is at iteration k + 1, reading population rows s - 5 .. s - 3
-// (nine rows in flight in all: D's three, A's three, two copies and the row
-// D of iteration k - 1 read).  Before leaving iteration k the front waits
-// for D of iteration k - 1, so that in iteration k + 1 nothing it writes --
-// ring A row s, grad rho^N and n-hat rows s - 1, G and u rows s - 2, the
-// copy into the slot of row s - 6 -- is still being read; the mirrored wall
-// rows ny of n-hat and u have slots of their own.
+// the copies, issue the next one and run A and B of iteration k, then
+// publish them with bar.arrive; the back threads run C and D of iteration k
+// (a back-only barrier between them) while the front is at iteration k + 1.
+// D reads population rows s - 5 .. s - 3 (nine rows in flight in all: D's
+// three, A's three, two copies and the row D of iteration k - 1 read).
+// Before leaving iteration k the front waits for C and D of iteration k - 1,
+// so that in iteration k + 1 nothing it writes -- ring A row s, grad rho^N
+// and n-hat rows s - 1, the copy into the slot of row s - 6 -- is still
+// being read; the mirrored wall row ny of n-hat has a slot of its own, and
+// so has u's, written and read by the back alone.
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsigned pop_addr, const char* __restrict__ src,
                                            char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
@@ -680,10 +682,8 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             stage_a(s, ks);
             bar_sync<kBarFront, kThreads>();
             stage_b(s);
-            bar_sync<kBarFront, kThreads>();
-            stage_c(s);
-            // publish A-C of iteration k, then wait until D of iteration k - 1
-            // is done with the rows that iteration k + 1 overwrites
+            // publish A and B of iteration k, then wait until C and D of
+            // iteration k - 1 are done with the rows that iteration k + 1 overwrites
             if (k & 1) {
                 bar_arrive<kBarC + 1, kStepThreads>();
                 bar_sync<kBarD + 1, kStepThreads>();
@@ -699,6 +699,8 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
         for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
             if (k & 1) bar_sync<kBarC + 1, kStepThreads>();
             else bar_sync<kBarC, kStepThreads>();
+            stage_c(s_first + k);
+            bar_sync<kBarBack, kThreads>();  // u of row s - 3 is in shared memory
             stage_d(s_first + k, ks);
             if (k + 1 < iters) {
                 if (k & 1) bar_arrive<kBarD, kStepThreads>();  // D of iteration k + 1 (even) may follow
