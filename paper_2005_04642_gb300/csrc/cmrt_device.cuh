@@ -166,12 +166,22 @@ __device__ __forceinline__ void store_recoloured_f32(float* out, size_t nodes, c
     segregation(smin * sx, smin * sy, seg);
     float* out_min = out + (red_major ? 9 * nodes : 0);
     float* out_maj = out + (red_major ? 0 : 9 * nodes);
+    // links in pairs as packed FP32x2 FMAs (fp - cmin as cmin * -1 + fp: the
+    // same single rounding as the subtraction)
+    const float2 a2 = make_float2(amin, amin), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const float cmin = fmaf(amin, fp[i], seg[i]);
-        __stcs(out_min + i * nodes, cmin);
-        __stcs(out_maj + i * nodes, fp[i] - cmin);
+    for (int i = 0; i < 8; i += 2) {
+        const float2 f2 = make_float2(fp[i], fp[i + 1]);
+        const float2 cmin = __ffma2_rn(a2, f2, make_float2(seg[i], seg[i + 1]));
+        const float2 cmaj = __ffma2_rn(cmin, m1, f2);
+        __stcs(out_min + i * nodes, cmin.x);
+        __stcs(out_min + (i + 1) * nodes, cmin.y);
+        __stcs(out_maj + i * nodes, cmaj.x);
+        __stcs(out_maj + (i + 1) * nodes, cmaj.y);
     }
+    const float cmin8 = fmaf(amin, fp[8], seg[8]);
+    __stcs(out_min + 8 * nodes, cmin8);
+    __stcs(out_maj + 8 * nodes, fp[8] - cmin8);
 }
 
 }  // namespace cmrt

@@ -206,6 +206,7 @@ struct Layout16 {
 
     __device__ __forceinline__ static float2 to2(H v);
     __device__ __forceinline__ static H from2(float a, float b);
+    __device__ __forceinline__ static H from2x(float2 v) { return from2(v.x, v.y); }
 
     template <bool VEC>
     struct Plan {
@@ -276,9 +277,10 @@ struct Layout16 {
                                                 float& b) {
         const float2 rho = reinterpret_cast<const float2*>(slot)[col];
         const H d = reinterpret_cast<const H*>(slot + kRhoBytes + i * kDevBytes)[col];
-        const float2 dv = to2(d);
-        r = fmaf(rho.x, psi_r(i, P), dv.x);
-        b = fmaf(rho.y, psi_b(i, P), dv.y);
+        // (R_i, B_i) = (rho'_R psi^R_i, rho'_B psi^B_i) + d_i as one packed FP32x2 FMA
+        const float2 c = __ffma2_rn(rho, make_float2(psi_r(i, P), psi_b(i, P)), to2(d));
+        r = c.x;
+        b = c.y;
     }
 
     __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
@@ -291,18 +293,18 @@ struct Layout16 {
         // the stored densities absorb the rounding of the deviations, so that the
         // decoded populations of the record sum to rho_R and rho_B (colour mass is
         // conserved as with FP32 storage): rho'_C = rho_C - sum_i round(d_C,i)
-        float er = 0.0f, eb = 0.0f;
+        // packed FP32x2 arithmetic on the (red, blue) pair of each link, lane by
+        // lane the same roundings as the scalar form
+        float2 e = make_float2(0.0f, 0.0f);
+        const float2 a2 = make_float2(aR, aB), mrho = make_float2(-rr, -rb);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float R = fmaf(aR, fp[i], seg[i]);
-            const float B = fmaf(aB, fp[i], -seg[i]);
-            const H h = from2(fmaf(-rr, psi_r(i, P), R), fmaf(-rb, psi_b(i, P), B));
-            const float2 back = to2(h);
-            er += back.x;
-            eb += back.y;
+            const float2 C = __ffma2_rn(a2, make_float2(fp[i], fp[i]), make_float2(seg[i], -seg[i]));
+            const H h = from2x(__ffma2_rn(mrho, make_float2(psi_r(i, P), psi_b(i, P)), C));
+            e = __fadd2_rn(e, to2(h));
             dev[i * nodes] = h;
         }
-        reinterpret_cast<float2*>(dst)[node] = make_float2(rr - er, rb - eb);
+        reinterpret_cast<float2*>(dst)[node] = make_float2(rr - e.x, rb - e.y);
     }
 };
 
