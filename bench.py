@@ -198,6 +198,23 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest `value` over all ranks (the slowest rank's time): an
+    all-reduce with MAX when a process group is up, else the value itself."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells, steps, world, seconds):
+    """Whole-job throughput: every rank steps its own replica of `cells`
+    nodes `steps` times, all within `seconds` (the max over ranks)."""
+    return world * cells * steps / seconds / 1e6
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_cmrt(args, rank, world, local_rank):
     import torch
@@ -240,11 +257,8 @@ def run_cmrt(args, rank, world, local_rank):
     lat.close()
     del lat
     torch.cuda.empty_cache()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_mlups(cells, args.steps, world, ms_max * 1e-3)
     per_launch_s = (ms / args.steps) * 1e-3
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -264,10 +278,7 @@ def run_cmrt(args, rank, world, local_rank):
     barrier()
     e2e_s = time.perf_counter() - t0
     cm.cmrt_destroy(ctx)
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * args.steps / float(te.item()) / 1e6
+    e2e_value = whole_job_mlups(cells, args.steps, world, max_over_ranks(e2e_s, dist, "cuda"))
     h2d = (h_rn.numel() + h_u.numel()) * 4
     d2h = sum(o.numel() for o in h_out) * 4
 
