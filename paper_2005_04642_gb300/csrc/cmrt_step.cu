@@ -105,10 +105,7 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ float sum9(const float (&v)[9]) {
-    return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-}
-// (sum9(r), sum9(b)) in the same order, as packed FP32x2 adds (one instruction per pair)
+// (sum over links of r, of b), pairwise, as packed FP32x2 adds (one instruction per pair)
 __device__ __forceinline__ float2 sum9x2(const float (&r)[9], const float (&b)[9]) {
     float2 v[9];
 #pragma unroll
