@@ -639,6 +639,265 @@ __global__ void __launch_bounds__(kAT) k_rev_expand(const StepParams P, const fl
     }
 }
 
+// ----------------------------------------------------------------- fused tail of the reverse step
+// The reverse of the force, of the normal, of the moments and the transposed
+// gather (or, for the step VJP, the expansion at the node) in one row
+// wavefront, compact stencils only.  A CTA owns the strip [x0, x0 + 120) of
+// the rows [y0, y0 + rows), with 4 halo columns on each side (one thread per
+// window column), and marches down the rows; iteration k (s = y0 - 4 + k)
+// runs
+//   L  (row s)      load div-u-bar into a ring
+//   R2 (row s - 1)  reverse of div u, u = (j + G/2) / rho and G          (k_rev_force)
+//   R3 (row s - 2)  reverse of K = div n-hat and of n-hat                 (k_rev_normal)
+//   R4 (row s - 3)  reverse of grad rho^N, grad Phi', rho^N, Phi', j      (k_rev_moments)
+//   R5 (row s - 4)  lambda of P_{t-1}: transposed gather or expansion    (k_rev_gather / k_rev_expand)
+// with one barrier between stages.  Each stage reads its stencil inputs from
+// rings in shared memory, which hold exactly the rows still to be read, and
+// its per-node inputs from the planes, loaded into registers one iteration
+// ahead so that their latency overlaps the current row: every plane row is
+// read from HBM once and only lambda is written.  The arithmetic is that of
+// the plane passes, term by term in the same order.
+constexpr int kTailRows = 100;  // ring rows of shared memory, kWin floats each
+enum TailRing : int {
+    kTDivub = 0, kTKb = 4, kTJxb = 8, kTJyb = 12, kTGxb = 16, kTGyb = 20, kTDpxb = 24, kTDpyb = 28,
+    kTRr = 32, kTRb = 36, kTGx = 40, kTGy = 44,  // 4-row rings
+    kTRrb = 48, kTRbb = 56,                      // 8-row rings
+    kTFb = 64                                    // 9 links x 4 rows
+};
+constexpr int kTailSmem = kTailRows * kWin * 4;
+
+template <bool W, bool EXPAND>
+__global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const float* __restrict__ S,
+                                                   float* __restrict__ lam, const int rows,
+                                                   double* __restrict__ partials) {
+    extern __shared__ __align__(16) float tsm[];
+    const int t = threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const size_t n = static_cast<size_t>(nx) * ny;
+    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * rows;
+    const int y_end = min(y0 + rows, ny);
+    const int gx = wrap_to(x0 - kHalo + t, nx);  // this thread's lattice column
+    const bool own_col = t >= kHalo && t < kWin - kHalo && x0 + t - kHalo < nx;
+    auto row_ok = [&](int r) { return !W || (r >= 0 && r < ny); };
+    auto node = [&](int r) { return static_cast<size_t>(wrap_to(r, ny)) * nx + gx; };
+    auto ring4 = [&](int base, int r) { return tsm + (base + (r & 3)) * kWin; };
+    auto ring8 = [&](int base, int r) { return tsm + (base + (r & 7)) * kWin; };
+    auto fbr = [&](int i, int r) { return tsm + (kTFb + 4 * i + (r & 3)) * kWin; };
+    // transpose of one component of the compact gradient, on ring rows
+    // (the tap order and wall terms of Nbh::gradT)
+    auto gradT = [&](auto rowp, bool xc, int y, float parity) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int c = xc ? lcx(i) : lcy(i);
+            if (c == 0) continue;
+            const float k = 3.0f * lw(i) * float(c);
+            const int dx = -lcx(i), dy = -lcy(i);
+            if (!W) {
+                acc = fmaf(k, rowp(y + dy)[t + dx], acc);
+            } else {
+                if (y + dy >= 0 && y + dy < ny) acc = fmaf(k, rowp(y + dy)[t + dx], acc);
+                const int yb = -1 - y + dy;
+                if (yb >= 0 && yb < ny && yb - dy < 0) acc = fmaf(parity * k, rowp(yb)[t + dx], acc);
+                const int yt = 2 * ny - 1 - y + dy;
+                if (yt >= 0 && yt < ny && yt - dy >= ny) acc = fmaf(parity * k, rowp(yt)[t + dx], acc);
+            }
+        }
+        return acc;
+    };
+    double acc_sigma = 0.0, acc_gx = 0.0, acc_gy = 0.0;
+    const int iters = (y_end - y0) + 8;
+    // per-node inputs, one row ahead: div-u-bar for L, 17 planes for R2, 10 for R4
+    constexpr int kIn2[17] = {kUXB, kUYB, kRR, kRB, kUX, kUY, kGFXB, kGFYB, kGX, kGY, kK,
+                              kGXB, kGYB, kRRB, kRBB, kDPXB, kDPYB};
+    auto in_L = [&](int r) { return row_ok(r); };
+    auto in_R2 = [&](int r) { return r >= y0 - 3 && r <= y_end + 2 && row_ok(r) && t >= 1 && t < kWin - 1; };
+    auto in_R4 = [&](int r) { return r >= y0 - 1 && r <= y_end && row_ok(r) && t >= 3 && t < kWin - 3; };
+    float dv_next = 0.0f, in2_next[17], in4_next[10];
+    auto fetch = [&](int s) {  // the inputs of iteration s: L at s, R2 at s - 1, R4 at s - 3
+        if (in_L(s)) dv_next = S[kDIVUB * n + node(s)];
+        if (in_R2(s - 1)) {
+            const size_t o = node(s - 1);
+#pragma unroll
+            for (int j = 0; j < 17; ++j) in2_next[j] = S[static_cast<size_t>(kIn2[j]) * n + o];
+        }
+        if (in_R4(s - 3)) {
+            const size_t o = node(s - 3);
+            in4_next[0] = S[kRNB * n + o];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) in4_next[1 + i] = S[static_cast<size_t>(kFB0 + i) * n + o];
+        }
+    };
+    fetch(y0 - 4);
+    for (int k = 0; k < iters; ++k) {
+        const int s = y0 - 4 + k;
+        const float dv = dv_next;
+        float in2[17], in4[10];
+#pragma unroll
+        for (int j = 0; j < 17; ++j) in2[j] = in2_next[j];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) in4[j] = in4_next[j];
+        if (k + 1 < iters) fetch(s + 1);
+        // ---- L: div-u-bar of row s (the window: R2 reads it at t +- 1)
+        if (in_L(s)) ring4(kTDivub, s)[t] = dv;
+        __syncthreads();
+        // ---- R2: reverse of the force at row s - 1 (k_rev_force)
+        {
+            const int y = s - 1;
+            if (in_R2(y)) {
+                const auto dvr = [&](int r) { return ring4(kTDivub, r); };
+                const float uxt = in2[0] + gradT(dvr, true, y, -1.0f);
+                const float uyt = in2[1] + gradT(dvr, false, y, -1.0f);
+                const float rr = in2[2], rb = in2[3];
+                const float rho = rr + rb;
+                const float ir = 1.0f / rho;
+                const float ux = in2[4], uy = in2[5];
+                const float Gxt = fmaf(0.5f * ir, uxt, in2[6]);
+                const float Gyt = fmaf(0.5f * ir, uyt, in2[7]);
+                const float gxv = in2[8], gyv = in2[9], K = in2[10];
+                const float rhob = -(ux * uxt + uy * uyt) * ir + Gxt * P.gacc_x + Gyt * P.gacc_y;
+                const float gG = fmaf(Gxt, gxv, Gyt * gyv);
+                ring4(kTJxb, y)[t] = uxt * ir;
+                ring4(kTJyb, y)[t] = uyt * ir;
+                ring4(kTKb, y)[t] = P.half_sigma * gG;
+                float gxb = in2[11], gyb = in2[12], rrb = in2[13], rbb = in2[14];
+                gxb += P.half_sigma * K * Gxt;
+                gyb += P.half_sigma * K * Gyt;
+                rrb += rhob;
+                rbb += rhob;
+                ring4(kTGxb, y)[t] = gxb;
+                ring4(kTGyb, y)[t] = gyb;
+                ring8(kTRrb, y)[t] = rrb;
+                ring8(kTRbb, y)[t] = rbb;
+                ring4(kTDpxb, y)[t] = in2[15];
+                ring4(kTDpyb, y)[t] = in2[16];
+                ring4(kTRr, y)[t] = rr;
+                ring4(kTRb, y)[t] = rb;
+                ring4(kTGx, y)[t] = gxv;
+                ring4(kTGy, y)[t] = gyv;
+                if (own_col && y >= y0 && y < y_end) {
+                    acc_sigma += static_cast<double>(0.5f * K * gG);
+                    acc_gx += static_cast<double>(rho * Gxt);
+                    acc_gy += static_cast<double>(rho * Gyt);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- R3: reverse of K = div n-hat and of the regularised normal at row s - 2 (k_rev_normal)
+        if (P.curvature_mode == 0) {
+            const int y = s - 2;
+            if (y >= y0 - 2 && y <= y_end + 1 && row_ok(y) && t >= 2 && t < kWin - 2) {
+                const auto kb = [&](int r) { return ring4(kTKb, r); };
+                const float nxb = gradT(kb, true, y, 1.0f);
+                const float nyb = gradT(kb, false, y, -1.0f);
+                float tx, ty;
+                normalise_T(ring4(kTGx, y)[t], ring4(kTGy, y)[t], nxb, nyb, tx, ty);
+                ring4(kTGxb, y)[t] -= tx;
+                ring4(kTGyb, y)[t] -= ty;
+            }
+        }
+        __syncthreads();
+        // ---- R4: reverse of the gradients, rho^N, Phi' and the moments at row s - 3 (k_rev_moments)
+        {
+            const int y = s - 3;
+            if (in_R4(y)) {
+                float rnb = in4[0];
+                rnb += gradT([&](int r) { return ring4(kTGxb, r); }, true, y, 1.0f) +
+                       gradT([&](int r) { return ring4(kTGyb, r); }, false, y, 1.0f);
+                const float phb = gradT([&](int r) { return ring4(kTDpxb, r); }, true, y, 1.0f) +
+                                  gradT([&](int r) { return ring4(kTDpyb, r); }, false, y, 1.0f);
+                const float rr = ring4(kTRr, y)[t], rb = ring4(kTRb, y)[t];
+                const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
+                const float iden = 1.0f / ((a + b) * (a + b));
+                ring8(kTRrb, y)[t] += fmaf(rnb * 2.0f * b * iden, P.inv_rho0_r, phb * P.phip_r);
+                ring8(kTRbb, y)[t] += fmaf(rnb * -2.0f * a * iden, P.inv_rho0_b, phb * P.phip_b);
+                const float jxb = ring4(kTJxb, y)[t], jyb = ring4(kTJyb, y)[t];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    float v = in4[1 + i];
+                    if (lcx(i)) v += float(lcx(i)) * jxb;
+                    if (lcy(i)) v += float(lcy(i)) * jyb;
+                    fbr(i, y)[t] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- R5: lambda at row s - 4 (k_rev_gather / k_rev_expand)
+        {
+            const int y = s - 4;
+            if (y >= y0 && y < y_end && own_col) {
+                const size_t o = static_cast<size_t>(y) * nx + gx;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    float common, cr, cb;
+                    if (EXPAND) {
+                        common = fbr(i, y)[t];
+                        cr = ring8(kTRrb, y)[t];
+                        cb = ring8(kTRbb, y)[t];
+                    } else {
+                        int li = i, sy = y + lcy(i), st = t + lcx(i);
+                        if (W && (sy < 0 || sy >= ny)) {  // the node's own reversed link (half-way bounce-back)
+                            li = lopp(i);
+                            sy = y;
+                            st = t;
+                        }
+                        common = fbr(li, sy)[st];
+                        cr = ring8(kTRrb, sy)[st];
+                        cb = ring8(kTRbb, sy)[st];
+                    }
+                    lam[static_cast<size_t>(i) * n + o] = common + cr;
+                    lam[static_cast<size_t>(9 + i) * n + o] = common + cb;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // parameter gradients of the owned nodes: FP64 per thread, then per CTA
+    __shared__ double red[kWin / 32][3];
+    double v[3] = {acc_sigma, acc_gx, acc_gy};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+    if ((t & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) red[t >> 5][j] = v[j];
+    __syncthreads();
+    if (t < 3) {
+        double a = 0.0;
+        for (int w = 0; w < kWin / 32; ++w) a += red[w][t];
+        const int slot = t == 0 ? 0 : (t == 1 ? 4 : 5);  // sigma, g_acc_x, g_acc_y
+        partials[(static_cast<size_t>(blockIdx.y) * gridDim.x + blockIdx.x) * kAdjSlots + slot] += a;
+    }
+}
+
+// rows per CTA of the fused tail: enough CTAs for two waves of 152 SMs where
+// the lattice allows, at most 64 rows (8 fill iterations per segment)
+int tail_rows(int nx, int ny) {
+    const long strips = (nx + kTileX - 1) / kTileX;
+    int rows = 64;
+    while (rows > 4 && strips * ((ny + rows - 1) / rows) < 2 * 152) rows /= 2;
+    return rows;
+}
+
+template <bool W, bool EXPAND>
+cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double* partials, cudaStream_t s) {
+    static unsigned long long configured = 0;  // the shared-memory opt-in, once per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(k_rev_tail<W, EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    const int rows = tail_rows(P.nx, P.ny);
+    const dim3 g(static_cast<unsigned>((P.nx + kTileX - 1) / kTileX), static_cast<unsigned>((P.ny + rows - 1) / rows));
+    k_rev_tail<W, EXPAND><<<g, kWin, kTailSmem, s>>>(P, S, lam, rows, partials);
+    return cudaGetLastError();
+}
+
 // Objective J = 1/2 sum (rho^N - target)^2 of f(T) = gather(P_{T-1}) and its
 // gradient dJ/dC_i = (rho^N - target) d rho^N / d rho_C, the same for every link.
 template <bool W>
@@ -854,21 +1113,34 @@ void forward_planes(const float* post, const StepParams& P, float* S, cudaStream
     k_fwd_force<W><<<g, kAT, 0, s>>>(P, S);
 }
 
-// the reverse passes shared by both forms of one adjoint step
-template <int O, bool W>
-void reverse_core(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
-                  cudaStream_t s) {
+// the reverse passes shared by both forms of one adjoint step; with the
+// compact stencil (O = 2) the passes after the collision are one fused launch
+// (k_rev_tail), which also writes lambda: `lam_out` is lambda of P_{t-1}
+// (transposed gather) or, with EXPAND, dJ/df(t) in the public layout
+template <int O, bool W, bool EXPAND>
+cudaError_t reverse_step(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
+                         float* lam_out, cudaStream_t s) {
     const dim3 g = adj_grid(P);
     forward_planes<O, W>(post, P, S, s);
     k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
+    if (O == 2) return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
     k_rev_force<W><<<g, kAT, 0, s>>>(P, S, partials);
     if (P.curvature_mode == 0) k_rev_normal<W><<<g, kAT, 0, s>>>(P, S);
     k_rev_moments<O, W><<<g, kAT, 0, s>>>(P, S);
+    if (EXPAND) k_rev_expand<<<g, kAT, 0, s>>>(P, S, lam_out);
+    else k_rev_gather<W><<<g, kAT, 0, s>>>(P, S, lam_out);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-int adj_blocks(int nx, int ny) { return ((nx + kAT - 1) / kAT) * ny; }
+int adj_blocks(int nx, int ny) {
+    // per-CTA partial-sum slots: the larger of the plane passes' grid and the fused tail's
+    const int planes = ((nx + kAT - 1) / kAT) * ny;
+    const int rows = tail_rows(nx, ny);
+    const int tail = ((nx + kTileX - 1) / kTileX) * ((ny + rows - 1) / rows);
+    return planes > tail ? planes : tail;
+}
 
 cudaError_t launch_step_planes(const float* post, float* dst, const StepParams& P, float* scratch, unsigned* flag,
                                cudaStream_t s) {
@@ -893,24 +1165,27 @@ cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* sc
     return cudaGetLastError();
 }
 
-int adj_launches_per_step(const StepParams& P) { return P.curvature_mode == 0 ? 8 : 7; }
+int adj_launches_per_step(const StepParams& P) {
+    if (P.stencil_order == 2) return 5;  // three forward passes, the collision, the fused tail
+    return P.curvature_mode == 0 ? 8 : 7;
+}
 
 cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                 double* partials, float* lam_prev, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     dispatch(P, [&](auto o, auto w) {
-        reverse_core<decltype(o)::value, decltype(w)::value>(post, lam_post, P, scratch, partials, s);
-        k_rev_gather<decltype(w)::value><<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_prev);
+        e = reverse_step<decltype(o)::value, decltype(w)::value, false>(post, lam_post, P, scratch, partials, lam_prev, s);
     });
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                     double* partials, float* lam_pre, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     dispatch(P, [&](auto o, auto w) {
-        reverse_core<decltype(o)::value, decltype(w)::value>(post, lam_post, P, scratch, partials, s);
+        e = reverse_step<decltype(o)::value, decltype(w)::value, true>(post, lam_post, P, scratch, partials, lam_pre, s);
     });
-    k_rev_expand<<<adj_grid(P), kAT, 0, s>>>(P, scratch, lam_pre);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_seed(const float* post, const float* target, const StepParams& P, float* scratch,

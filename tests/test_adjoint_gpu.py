@@ -53,13 +53,19 @@ VJP_CASES = [
     ("walls_gravity", dict(wall_y=True, g_acc=(2e-4, -3e-4))),
     ("rates_ghostN", dict(lambda3_r=1.5, lambda3_b=0.7, lambda6=1.2, lambda7=0.8, ghost_N_mode=1)),
     ("visc_eta_fixedK", dict(visc_mode=1, eta=0.2, curvature_mode=1, fixed_K=0.05, g_vol=(1e-4, 0.0))),
-    ("ragged_walls", dict(wall_y=True, sigma=0.02)),
+    ("ragged_walls", dict(wall_y=True, sigma=0.02, size=(131, 37))),
+    # the fused reverse tail's tiling: a lattice narrower than its 128-column
+    # window and shorter than a row segment; three strips of many 4-row
+    # segments, so that every strip and segment seam is crossed
+    ("tiny_periodic", dict(size=(5, 4))),
+    ("multi_segment", dict(size=(250, 70), g_acc=(1e-4, 2e-4))),
 ]
 
 
 @pytest.mark.parametrize("name,kw", VJP_CASES)
 def test_step_vjp_matches_oracle_adjoint(name, kw):
-    nx, ny = (131, 37) if name == "ragged_walls" else (40, 24)
+    kw = dict(kw)
+    nx, ny = kw.pop("size", (40, 24))
     d = I.base_params(nx, ny, sigma=kw.pop("sigma", 0.01), **kw)
     p = O.Params(**d)
     R, B = _state32(d, seed=3)
