@@ -880,6 +880,13 @@ int tail_rows(int nx, int ny) {
     return rows;
 }
 
+// fused tail or plane passes (compact stencil): as asked, else the fused
+// kernel where the lattice fills 16-row segments in two waves -- on smaller
+// lattices its 8 fill rows per segment cost more than the launches it saves
+bool use_tail(const StepParams& P) {
+    return P.adjoint_tail == 1 || (P.adjoint_tail == 0 && tail_rows(P.nx, P.ny) >= 16);
+}
+
 template <bool W, bool EXPAND>
 cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double* partials, cudaStream_t s) {
     static unsigned long long configured = 0;  // the shared-memory opt-in, once per device
@@ -1123,7 +1130,7 @@ cudaError_t reverse_step(const float* post, const float* lam_post, const StepPar
     const dim3 g = adj_grid(P);
     forward_planes<O, W>(post, P, S, s);
     k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
-    if (O == 2) return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
+    if (O == 2 && use_tail(P)) return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
     k_rev_force<W><<<g, kAT, 0, s>>>(P, S, partials);
     if (P.curvature_mode == 0) k_rev_normal<W><<<g, kAT, 0, s>>>(P, S);
     k_rev_moments<O, W><<<g, kAT, 0, s>>>(P, S);
@@ -1166,7 +1173,7 @@ cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* sc
 }
 
 int adj_launches_per_step(const StepParams& P) {
-    if (P.stencil_order == 2) return 5;  // three forward passes, the collision, the fused tail
+    if (P.stencil_order == 2 && use_tail(P)) return 5;  // three forward passes, the collision, the fused tail
     return P.curvature_mode == 0 ? 8 : 7;
 }
 

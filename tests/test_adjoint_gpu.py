@@ -62,14 +62,15 @@ VJP_CASES = [
 ]
 
 
+@pytest.mark.parametrize("tail", [1, 2], ids=["fused_tail", "plane_passes"])
 @pytest.mark.parametrize("name,kw", VJP_CASES)
-def test_step_vjp_matches_oracle_adjoint(name, kw):
+def test_step_vjp_matches_oracle_adjoint(name, kw, tail):
     kw = dict(kw)
     nx, ny = kw.pop("size", (40, 24))
     d = I.base_params(nx, ny, sigma=kw.pop("sigma", 0.01), **kw)
     p = O.Params(**d)
     R, B = _state32(d, seed=3)
-    lat = cm.Lattice(d, None, None)
+    lat = cm.Lattice(dict(d, adjoint_tail=tail), None, None)
     lat.set_populations(np.stack([R, B]))
     rng = np.random.default_rng(4)
     lam_next = rng.standard_normal((2, 9, ny, nx)).astype(np.float32)
@@ -156,6 +157,27 @@ def test_adjoint_gradient_matches_oracle(wall):
     for name_ in PN:
         assert abs(g[name_] - g_ref[name_]) <= 3e-3 * abs(g_ref[name_]) + 1e-4 * gmax, (name_, g[name_], g_ref[name_])
     assert np.abs(grn - grn_ref).max() <= 3e-3 * np.abs(grn_ref).max()
+
+
+@pytest.mark.parametrize("wall", [False, True])
+def test_fused_tail_equals_plane_passes(wall):
+    """The whole checkpointed adjoint through the fused reverse tail and
+    through the four plane passes it replaces: the same objective and, up to
+    the summation order of the FP32 partial sums, the same gradients."""
+    nsteps = 12
+    d, rn0, u0, target = _drop_setup(96, 20.0, nsteps, g=1e-4, wall=wall)
+    outs = []
+    for tail in (1, 2):
+        lat = cm.Lattice(dict(d, adjoint_tail=tail), rn0.astype(np.float32), None)
+        J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=5, want_rho_n0=True)
+        outs.append((J, g, grn.double().cpu().numpy()))
+        lat.close()
+    (J1, g1, r1), (J2, g2, r2) = outs
+    assert J1 == J2
+    gmax = max(abs(v) for v in g2.values())
+    for k in g2:
+        assert abs(g1[k] - g2[k]) <= 1e-5 * abs(g2[k]) + 1e-7 * gmax, (k, g1[k], g2[k])
+    assert np.abs(r1 - r2).max() <= 1e-5 * np.abs(r2).max()
 
 
 def test_checkpoint_interval_gives_identical_gradients():
