@@ -98,12 +98,13 @@ typedef struct {
                                 (synchronising the stream then); 0 = only at cmrt_diagnostics    */
     int32_t precision_reference; /* 16-bit storage reference psi^C_i: 0 = phi_i of pure colour C
                                 (Eq. eq_phi at alpha_C); 1 = the lattice weights w_i            */
-    int32_t adjoint_tail;    /* the reverse step after its collision pass (compact stencil only;
-                                App. B's stencil always uses plane passes): 0 = automatic -- one
-                                fused row-wavefront kernel where the lattice fills 16-row segments
-                                in two waves of the GPU, four plane passes on smaller lattices;
-                                1 = always the fused kernel; 2 = always the plane passes.  Both
-                                compute the same values (rounding order aside)                  */
+    int32_t adjoint_fused;   /* kernels of one reverse step of cmrt_adjoint / cmrt_step_vjp
+                                (compact stencil; App. B's stencil always uses plane passes):
+                                0 = automatic -- two fused row-wavefront kernels where the lattice
+                                fills 16-row segments in two waves of the GPU, eight per-node
+                                plane passes on smaller lattices; 1 = always the fused kernels;
+                                2 = always the plane passes.  Both compute the same values
+                                (rounding order aside)                                          */
 } cmrt_params;
 
 /* ABI version of the loaded library (CMRT_ABI_VERSION). */

@@ -33,7 +33,7 @@ class cmrt_params(ctypes.Structure):
         ("stencil_order", ctypes.c_int32), ("curvature_mode", ctypes.c_int32),
         ("fixed_K", ctypes.c_double), ("ghost_N_mode", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("diag_every", ctypes.c_int32),
-        ("precision_reference", ctypes.c_int32), ("adjoint_tail", ctypes.c_int32),
+        ("precision_reference", ctypes.c_int32), ("adjoint_fused", ctypes.c_int32),
     ]
 
 

@@ -189,8 +189,8 @@ cmrt_status validate(const cmrt_params* p) {
         return fail(nullptr, CMRT_EINVAL, "precision must be 0 (FP32), 1 (BF16) or 2 (FP16)");
     if (p->precision_reference != 0 && p->precision_reference != 1)
         return fail(nullptr, CMRT_EINVAL, "precision_reference must be 0 or 1");
-    if (p->adjoint_tail < 0 || p->adjoint_tail > 2)
-        return fail(nullptr, CMRT_EINVAL, "adjoint_tail must be 0 (automatic), 1 (fused) or 2 (plane passes)");
+    if (p->adjoint_fused < 0 || p->adjoint_fused > 2)
+        return fail(nullptr, CMRT_EINVAL, "adjoint_fused must be 0 (automatic), 1 (fused kernels) or 2 (plane passes)");
     if (p->diag_every < 0) return fail(nullptr, CMRT_EINVAL, "diag_every must be >= 0");
     return CMRT_OK;
 }
@@ -204,7 +204,7 @@ StepParams derive(const cmrt_params& p) {
     s.curvature_mode = p.curvature_mode;
     s.ghost_N_mode = p.ghost_N_mode;
     s.stencil_order = p.stencil_order;
-    s.adjoint_tail = p.adjoint_tail;
+    s.adjoint_fused = p.adjoint_fused;
     const double Lam = p.rho0_r / p.rho0_b;
     s.inv_rho0_r = static_cast<float>(1.0 / p.rho0_r);
     s.inv_rho0_b = static_cast<float>(1.0 / p.rho0_b);

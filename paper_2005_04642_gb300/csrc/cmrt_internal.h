@@ -21,7 +21,7 @@ struct StepParams {
     float psi_r[3], psi_b[3];      // 16-bit storage reference weights (rest, axis, diagonal)
     int visc_mode, curvature_mode, ghost_N_mode;
     int stencil_order;             // 2: compact gradients; 6: App. B for grad rho^N and grad Phi'
-    int adjoint_tail;              // 0: automatic, 1: fused reverse tail, 2: plane passes
+    int adjoint_fused;              // 0: automatic, 1: fused reverse tail, 2: plane passes
     float inv_rho0_r, inv_rho0_b;  // colour index (Eq. equ_rhoN_def)
     float alpha_r, alpha_b;        // rest weights phi_0 (Eq. eq_phi)
     float kphi_r, kphi_b;          // 9/5 (1 - alpha_C): phi_i = w_i (kphi_r rho_R + kphi_b rho_B) / rho

@@ -331,7 +331,204 @@ __global__ void __launch_bounds__(kAT) k_fwd_force(const StepParams P, float* __
 
 // ----------------------------------------------------------------- reverse passes
 // Reverse of the per-node collision and recolour (App. A Eqs. 38, eq84;
-// Eq. eq_re_color).  lam: adjoint of the post-collision state P_t (18 planes).
+// Eq. eq_re_color) at one node: the adjoints of the node's inputs from the
+// adjoint (lamr, lamb) of its post-collision populations.  Inputs: the
+// pre-collision populations f, the colour densities, the force-adjusted
+// velocity, the force, grad rho^N, rho^N, grad Phi' and div u.
+struct RevCollide {
+    float fbar[9];  // M^T m-bar: the common part of the population adjoint
+    float rrb, rbb, uxb, uyb, Gxb, Gyb, dPxb, dPyb, divub, gxb, gyb, rnb;
+    float acc[3];   // dJ/d(beta, lambda3_r, lambda3_b) of this node
+};
+__device__ __forceinline__ void rev_collide_node(const float (&f)[9], float rr, float rb, float ux, float uy, float Gx,
+                                                 float Gy, float gx, float gy, float rn, float dPx, float dPy,
+                                                 float divu, const float (&lamr)[9], const float (&lamb)[9],
+                                                 const StepParams& P, RevCollide& out) {
+    out.acc[0] = out.acc[1] = out.acc[2] = 0.0f;  // lambda3 terms stay 0 with constant eta
+    const float rho = rr + rb, ir = 1.0f / rho, ir2 = ir * ir;
+    // ---- forward values at this node
+    float nu, dnu_drn = 0.0f;
+    if (P.visc_mode == 0) {
+        nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
+        dnu_drn = 0.5f * (P.nu_r - P.nu_b);
+    } else {
+        nu = P.eta * ir;
+    }
+    const float lam3 = 2.0f / fmaf(6.0f, nu, 1.0f);
+    const float a = fmaf(-0.5f, lam3, 1.0f);
+    const float hx = Gx - dPx, hy = Gy - dPy;
+    const float iso = fmaf(ux, dPx, fmaf(uy, dPy, -rho * divu * (1.0f / 3.0f)));
+    const float Cxx = a * fmaf(2.0f * ux, hx, -iso);
+    const float Cyy = a * fmaf(2.0f * uy, hy, -iso);
+    const float Cxy = a * fmaf(ux, hy, uy * hx);
+    float m[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float h = p == 0 ? 1.0f : p == 1 ? float(lcx(i)) : p == 2 ? float(lcy(i))
+                          : p == 3 ? float(lcx(i) * lcx(i)) : p == 4 ? float(lcy(i) * lcy(i))
+                          : p == 5 ? float(lcx(i) * lcy(i)) : p == 6 ? lg(i)
+                          : p == 7 ? lg(i) * float(lcx(i)) : lg(i) * float(lcy(i));
+            if (h != 0.0f) s = fmaf(h, f[i], s);
+        }
+        m[p] = s;
+    }
+    const float pres = fmaf(P.cs2_r, rr, P.cs2_b * rb);
+    float meq[9] = {rho, rho * ux, rho * uy, fmaf(rho * ux, ux, pres), fmaf(rho * uy, uy, pres), rho * ux * uy,
+                    P.ghost_N_mode == 0 ? fmaf(P.neq_r, rr, P.neq_b * rb) : 0.0f, 0.0f, 0.0f};
+    const float lamv[9] = {0.0f, 0.0f, 0.0f, lam3, lam3, lam3, P.lambda6, P.lambda7, P.lambda7};
+    const float Sv[9] = {0.0f, Gx, Gy, Cxx, Cyy, Cxy, 0.0f, 0.0f, 0.0f};
+    float fp[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        float s = f[i];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const float k = kinv(i, p);
+            if (k != 0.0f) s = fmaf(k, fmaf(lamv[p], meq[p] - m[p], Sv[p]), s);
+        }
+        fp[i] = s;
+    }
+    const float mag2 = fmaf(gx, gx, gy * gy);
+    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    const float ex = gx * inv, ey = gy * inv;
+    const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * ir;  // phi_i = w_i phim (i != 0)
+    const float seg = P.beta * rr * rb * ir;
+    // ---- recolour: C++_i = x_C f+_i +/- seg phi_i (e . c-hat_i)
+    const float xR = rr * ir, xB = rb * ir;
+    float fpb[9];
+    float xRb = 0.0f, xBb = 0.0f, segb = 0.0f, phimb = 0.0f, exb = 0.0f, eyb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float lr = lamr[i];
+        const float lb = lamb[i];
+        fpb[i] = fmaf(xR, lr, xB * lb);
+        xRb = fmaf(lr, fp[i], xRb);
+        xBb = fmaf(lb, fp[i], xBb);
+        if (i > 0) {
+            const float db = lr - lb;
+            const float ec = fmaf(chx(i), ex, chy(i) * ey);
+            segb = fmaf(db * lw(i) * phim, ec, segb);
+            phimb = fmaf(db * seg * lw(i), ec, phimb);
+            exb = fmaf(db * seg * lw(i) * phim, chx(i), exb);
+            eyb = fmaf(db * seg * lw(i) * phim, chy(i), eyb);
+        }
+    }
+    out.acc[0] = segb * (rr * rb * ir);
+    float rrb = (xRb - xBb) * rb * ir2;
+    float rbb = (xBb - xRb) * rr * ir2;
+    rrb = fmaf(segb * P.beta, rb * rb * ir2, rrb);
+    rbb = fmaf(segb * P.beta, rr * rr * ir2, rbb);
+    rrb = fmaf(phimb * (P.kphi_r - P.kphi_b), rb * ir2, rrb);
+    rbb = fmaf(phimb * (P.kphi_b - P.kphi_r), rr * ir2, rbb);
+    float gxb, gyb;
+    normalise_T(gx, gy, exb, eyb, gxb, gyb);
+    // ---- reconstruction and relaxation: m+ = m + lambda (m^(0) - m) + S, f+ = M^{-1} m+
+    float mpb[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float k = kinv(i, p);
+            if (k != 0.0f) s = fmaf(k, fpb[i], s);
+        }
+        mpb[p] = s;
+    }
+    float lam3b = 0.0f;
+#pragma unroll
+    for (int p = 3; p < 6; ++p) lam3b = fmaf(mpb[p], meq[p] - m[p], lam3b);
+    float mb[9], meqb[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        mb[p] = (1.0f - lamv[p]) * mpb[p];
+        meqb[p] = lamv[p] * mpb[p];
+    }
+    // common part of the population adjoint, M^T m-bar
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float fbi = mb[0] + float(lcx(i)) * mb[1] + float(lcy(i)) * mb[2] +
+                          float(lcx(i) * lcx(i)) * mb[3] + float(lcy(i) * lcy(i)) * mb[4] +
+                          float(lcx(i) * lcy(i)) * mb[5] + lg(i) * (mb[6] + float(lcx(i)) * mb[7] +
+                                                                    float(lcy(i)) * mb[8]);
+        out.fbar[i] = fbi;
+    }
+    // modal equilibrium (App. A)
+    float rhob = meqb[0] + meqb[1] * ux + meqb[2] * uy + meqb[3] * ux * ux + meqb[4] * uy * uy +
+                 meqb[5] * ux * uy;
+    float uxb = rho * (meqb[1] + 2.0f * ux * meqb[3] + uy * meqb[5]);
+    float uyb = rho * (meqb[2] + 2.0f * uy * meqb[4] + ux * meqb[5]);
+    const float prb = meqb[3] + meqb[4];
+    rrb = fmaf(P.cs2_r, prb, rrb);
+    rbb = fmaf(P.cs2_b, prb, rbb);
+    if (P.ghost_N_mode == 0) {
+        rrb = fmaf(P.neq_r, meqb[6], rrb);
+        rbb = fmaf(P.neq_b, meqb[6], rbb);
+    }
+    // sources S = (0, G, C_xx, C_yy, C_xy, 0, 0, 0) and the correction tensor (Eq. Correction)
+    float Gxb = mpb[1], Gyb = mpb[2];
+    const float cxxb = mpb[3], cyyb = mpb[4], cxyb = mpb[5];
+    const float ab = cxxb * fmaf(2.0f * ux, hx, -iso) + cyyb * fmaf(2.0f * uy, hy, -iso) +
+                     cxyb * fmaf(ux, hy, uy * hx);
+    lam3b = fmaf(-0.5f, ab, lam3b);
+    const float isob = -a * (cxxb + cyyb);
+    const float hxb = a * fmaf(2.0f * ux, cxxb, uy * cxyb);
+    const float hyb = a * fmaf(2.0f * uy, cyyb, ux * cxyb);
+    uxb += a * fmaf(2.0f * hx, cxxb, hy * cxyb) + isob * dPx;
+    uyb += a * fmaf(2.0f * hy, cyyb, hx * cxyb) + isob * dPy;
+    Gxb += hxb;
+    Gyb += hyb;
+    const float dPxb = fmaf(isob, ux, -hxb);
+    const float dPyb = fmaf(isob, uy, -hyb);
+    rhob = fmaf(-isob * (1.0f / 3.0f), divu, rhob);
+    const float divub = -isob * rho * (1.0f / 3.0f);
+    // lambda_3 = 2 / (6 nu + 1): d lambda_3 / d nu = -3 lambda_3^2
+    const float nub = lam3b * (-3.0f * lam3 * lam3);
+    float rnb = 0.0f;
+    if (P.visc_mode == 0) {
+        rnb = nub * dnu_drn;
+        // nu_C = (2 / lambda3_C - 1) / 6: d nu_C / d lambda3_C = -(6 nu_C + 1)^2 / 12
+        const float dr = fmaf(6.0f, P.nu_r, 1.0f), db = fmaf(6.0f, P.nu_b, 1.0f);
+        out.acc[1] = nub * 0.5f * (1.0f + rn) * (-dr * dr * (1.0f / 12.0f));
+        out.acc[2] = nub * 0.5f * (1.0f - rn) * (-db * db * (1.0f / 12.0f));
+    } else {
+        rhob = fmaf(nub, -P.eta * ir2, rhob);
+    }
+    out.rrb = rrb + rhob;
+    out.rbb = rbb + rhob;
+    out.uxb = uxb;
+    out.uyb = uyb;
+    out.Gxb = Gxb;
+    out.Gyb = Gyb;
+    out.dPxb = dPxb;
+    out.dPyb = dPyb;
+    out.divub = divub;
+    out.gxb = gxb;
+    out.gyb = gyb;
+    out.rnb = rnb;
+}
+
+// the outputs of rev_collide_node into the planes at offset o
+__device__ __forceinline__ void store_rev_collide(float* __restrict__ S, size_t n, size_t o, const RevCollide& r) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) S[static_cast<size_t>(kFB0 + i) * n + o] = r.fbar[i];
+    S[kRRB * n + o] = r.rrb;
+    S[kRBB * n + o] = r.rbb;
+    S[kUXB * n + o] = r.uxb;
+    S[kUYB * n + o] = r.uyb;
+    S[kGFXB * n + o] = r.Gxb;
+    S[kGFYB * n + o] = r.Gyb;
+    S[kDPXB * n + o] = r.dPxb;
+    S[kDPYB * n + o] = r.dPyb;
+    S[kDIVUB * n + o] = r.divub;
+    S[kGXB * n + o] = r.gxb;
+    S[kGYB * n + o] = r.gyb;
+    S[kRNB * n + o] = r.rnb;
+}
+
+// The reverse collision pass: lam is the adjoint of the post-collision state P_t (18 planes).
 template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ post, const float* __restrict__ lam,
                                                       const StepParams P, float* __restrict__ S,
@@ -345,179 +542,23 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
         L.gather(post, fr, fb);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
-        const float rr = S[kRR * L.n + o], rb = S[kRB * L.n + o];
-        const float rho = rr + rb, ir = 1.0f / rho, ir2 = ir * ir;
-        const float ux = S[kUX * L.n + o], uy = S[kUY * L.n + o];
-        const float Gx = S[kGFX * L.n + o], Gy = S[kGFY * L.n + o];
-        const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
-        const float rn = S[kCHR * L.n + o] - S[kCHB * L.n + o];
         float dPx, dPy, dux, duy, t0, t1;
         L.template grad<ORDER>(S + kPHIP * L.n, 1.0f, dPx, dPy);
         L.template grad<2>(S + kUX * L.n, -1.0f, dux, t0);
         L.template grad<2>(S + kUY * L.n, -1.0f, t1, duy);
-        const float divu = dux + duy;
-        // ---- forward values at this node
-        float nu, dnu_drn = 0.0f;
-        if (P.visc_mode == 0) {
-            nu = fmaf(0.5f * (P.nu_r - P.nu_b), rn, 0.5f * (P.nu_r + P.nu_b));
-            dnu_drn = 0.5f * (P.nu_r - P.nu_b);
-        } else {
-            nu = P.eta * ir;
-        }
-        const float lam3 = 2.0f / fmaf(6.0f, nu, 1.0f);
-        const float a = fmaf(-0.5f, lam3, 1.0f);
-        const float hx = Gx - dPx, hy = Gy - dPy;
-        const float iso = fmaf(ux, dPx, fmaf(uy, dPy, -rho * divu * (1.0f / 3.0f)));
-        const float Cxx = a * fmaf(2.0f * ux, hx, -iso);
-        const float Cyy = a * fmaf(2.0f * uy, hy, -iso);
-        const float Cxy = a * fmaf(ux, hy, uy * hx);
-        float m[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float h = p == 0 ? 1.0f : p == 1 ? float(lcx(i)) : p == 2 ? float(lcy(i))
-                              : p == 3 ? float(lcx(i) * lcx(i)) : p == 4 ? float(lcy(i) * lcy(i))
-                              : p == 5 ? float(lcx(i) * lcy(i)) : p == 6 ? lg(i)
-                              : p == 7 ? lg(i) * float(lcx(i)) : lg(i) * float(lcy(i));
-                if (h != 0.0f) s = fmaf(h, f[i], s);
-            }
-            m[p] = s;
-        }
-        const float pres = fmaf(P.cs2_r, rr, P.cs2_b * rb);
-        float meq[9] = {rho, rho * ux, rho * uy, fmaf(rho * ux, ux, pres), fmaf(rho * uy, uy, pres), rho * ux * uy,
-                        P.ghost_N_mode == 0 ? fmaf(P.neq_r, rr, P.neq_b * rb) : 0.0f, 0.0f, 0.0f};
-        const float lamv[9] = {0.0f, 0.0f, 0.0f, lam3, lam3, lam3, P.lambda6, P.lambda7, P.lambda7};
-        const float Sv[9] = {0.0f, Gx, Gy, Cxx, Cyy, Cxy, 0.0f, 0.0f, 0.0f};
-        float fp[9];
+        float lr[9], lb[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            float s = f[i];
-#pragma unroll
-            for (int p = 0; p < 9; ++p) {
-                const float k = kinv(i, p);
-                if (k != 0.0f) s = fmaf(k, fmaf(lamv[p], meq[p] - m[p], Sv[p]), s);
-            }
-            fp[i] = s;
+            lr[i] = lam[static_cast<size_t>(i) * L.n + o];
+            lb[i] = lam[static_cast<size_t>(9 + i) * L.n + o];
         }
-        const float mag2 = fmaf(gx, gx, gy * gy);
-        const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
-        const float ex = gx * inv, ey = gy * inv;
-        const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * ir;  // phi_i = w_i phim (i != 0)
-        const float seg = P.beta * rr * rb * ir;
-        // ---- recolour: C++_i = x_C f+_i +/- seg phi_i (e . c-hat_i)
-        const float xR = rr * ir, xB = rb * ir;
-        float fpb[9];
-        float xRb = 0.0f, xBb = 0.0f, segb = 0.0f, phimb = 0.0f, exb = 0.0f, eyb = 0.0f;
+        RevCollide r;
+        rev_collide_node(f, S[kRR * L.n + o], S[kRB * L.n + o], S[kUX * L.n + o], S[kUY * L.n + o],
+                         S[kGFX * L.n + o], S[kGFY * L.n + o], S[kGX * L.n + o], S[kGY * L.n + o],
+                         S[kCHR * L.n + o] - S[kCHB * L.n + o], dPx, dPy, dux + duy, lr, lb, P, r);
+        store_rev_collide(S, L.n, o, r);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float lr = lam[static_cast<size_t>(i) * L.n + o];
-            const float lb = lam[static_cast<size_t>(9 + i) * L.n + o];
-            fpb[i] = fmaf(xR, lr, xB * lb);
-            xRb = fmaf(lr, fp[i], xRb);
-            xBb = fmaf(lb, fp[i], xBb);
-            if (i > 0) {
-                const float db = lr - lb;
-                const float ec = fmaf(chx(i), ex, chy(i) * ey);
-                segb = fmaf(db * lw(i) * phim, ec, segb);
-                phimb = fmaf(db * seg * lw(i), ec, phimb);
-                exb = fmaf(db * seg * lw(i) * phim, chx(i), exb);
-                eyb = fmaf(db * seg * lw(i) * phim, chy(i), eyb);
-            }
-        }
-        acc[0] = segb * (rr * rb * ir);
-        float rrb = (xRb - xBb) * rb * ir2;
-        float rbb = (xBb - xRb) * rr * ir2;
-        rrb = fmaf(segb * P.beta, rb * rb * ir2, rrb);
-        rbb = fmaf(segb * P.beta, rr * rr * ir2, rbb);
-        rrb = fmaf(phimb * (P.kphi_r - P.kphi_b), rb * ir2, rrb);
-        rbb = fmaf(phimb * (P.kphi_b - P.kphi_r), rr * ir2, rbb);
-        float gxb, gyb;
-        normalise_T(gx, gy, exb, eyb, gxb, gyb);
-        // ---- reconstruction and relaxation: m+ = m + lambda (m^(0) - m) + S, f+ = M^{-1} m+
-        float mpb[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float k = kinv(i, p);
-                if (k != 0.0f) s = fmaf(k, fpb[i], s);
-            }
-            mpb[p] = s;
-        }
-        float lam3b = 0.0f;
-#pragma unroll
-        for (int p = 3; p < 6; ++p) lam3b = fmaf(mpb[p], meq[p] - m[p], lam3b);
-        float mb[9], meqb[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            mb[p] = (1.0f - lamv[p]) * mpb[p];
-            meqb[p] = lamv[p] * mpb[p];
-        }
-        // common part of the population adjoint, M^T m-bar
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float fbi = mb[0] + float(lcx(i)) * mb[1] + float(lcy(i)) * mb[2] +
-                              float(lcx(i) * lcx(i)) * mb[3] + float(lcy(i) * lcy(i)) * mb[4] +
-                              float(lcx(i) * lcy(i)) * mb[5] + lg(i) * (mb[6] + float(lcx(i)) * mb[7] +
-                                                                        float(lcy(i)) * mb[8]);
-            S[static_cast<size_t>(kFB0 + i) * L.n + o] = fbi;
-        }
-        // modal equilibrium (App. A)
-        float rhob = meqb[0] + meqb[1] * ux + meqb[2] * uy + meqb[3] * ux * ux + meqb[4] * uy * uy +
-                     meqb[5] * ux * uy;
-        float uxb = rho * (meqb[1] + 2.0f * ux * meqb[3] + uy * meqb[5]);
-        float uyb = rho * (meqb[2] + 2.0f * uy * meqb[4] + ux * meqb[5]);
-        const float prb = meqb[3] + meqb[4];
-        rrb = fmaf(P.cs2_r, prb, rrb);
-        rbb = fmaf(P.cs2_b, prb, rbb);
-        if (P.ghost_N_mode == 0) {
-            rrb = fmaf(P.neq_r, meqb[6], rrb);
-            rbb = fmaf(P.neq_b, meqb[6], rbb);
-        }
-        // sources S = (0, G, C_xx, C_yy, C_xy, 0, 0, 0) and the correction tensor (Eq. Correction)
-        float Gxb = mpb[1], Gyb = mpb[2];
-        const float cxxb = mpb[3], cyyb = mpb[4], cxyb = mpb[5];
-        const float ab = cxxb * fmaf(2.0f * ux, hx, -iso) + cyyb * fmaf(2.0f * uy, hy, -iso) +
-                         cxyb * fmaf(ux, hy, uy * hx);
-        lam3b = fmaf(-0.5f, ab, lam3b);
-        const float isob = -a * (cxxb + cyyb);
-        const float hxb = a * fmaf(2.0f * ux, cxxb, uy * cxyb);
-        const float hyb = a * fmaf(2.0f * uy, cyyb, ux * cxyb);
-        uxb += a * fmaf(2.0f * hx, cxxb, hy * cxyb) + isob * dPx;
-        uyb += a * fmaf(2.0f * hy, cyyb, hx * cxyb) + isob * dPy;
-        Gxb += hxb;
-        Gyb += hyb;
-        const float dPxb = fmaf(isob, ux, -hxb);
-        const float dPyb = fmaf(isob, uy, -hyb);
-        rhob = fmaf(-isob * (1.0f / 3.0f), divu, rhob);
-        const float divub = -isob * rho * (1.0f / 3.0f);
-        // lambda_3 = 2 / (6 nu + 1): d lambda_3 / d nu = -3 lambda_3^2
-        const float nub = lam3b * (-3.0f * lam3 * lam3);
-        float rnb = 0.0f;
-        if (P.visc_mode == 0) {
-            rnb = nub * dnu_drn;
-            // nu_C = (2 / lambda3_C - 1) / 6: d nu_C / d lambda3_C = -(6 nu_C + 1)^2 / 12
-            const float dr = fmaf(6.0f, P.nu_r, 1.0f), db = fmaf(6.0f, P.nu_b, 1.0f);
-            acc[1] = nub * 0.5f * (1.0f + rn) * (-dr * dr * (1.0f / 12.0f));
-            acc[2] = nub * 0.5f * (1.0f - rn) * (-db * db * (1.0f / 12.0f));
-        } else {
-            rhob = fmaf(nub, -P.eta * ir2, rhob);
-        }
-        S[kRRB * L.n + o] = rrb + rhob;
-        S[kRBB * L.n + o] = rbb + rhob;
-        S[kUXB * L.n + o] = uxb;
-        S[kUYB * L.n + o] = uyb;
-        S[kGFXB * L.n + o] = Gxb;
-        S[kGFYB * L.n + o] = Gyb;
-        S[kDPXB * L.n + o] = dPxb;
-        S[kDPYB * L.n + o] = dPyb;
-        S[kDIVUB * L.n + o] = divub;
-        S[kGXB * L.n + o] = gxb;
-        S[kGYB * L.n + o] = gyb;
-        S[kRNB * L.n + o] = rnb;
+        for (int j = 0; j < 3; ++j) acc[j] = r.acc[j];
     }
     const int slots[3] = {1, 2, 3};
     add_partials<3>(acc, slots, partials);
@@ -880,11 +921,11 @@ int tail_rows(int nx, int ny) {
     return rows;
 }
 
-// fused tail or plane passes (compact stencil): as asked, else the fused
-// kernel where the lattice fills 16-row segments in two waves -- on smaller
-// lattices its 8 fill rows per segment cost more than the launches it saves
-bool use_tail(const StepParams& P) {
-    return P.adjoint_tail == 1 || (P.adjoint_tail == 0 && tail_rows(P.nx, P.ny) >= 16);
+// fused kernels or plane passes (compact stencil): as asked, else the fused
+// kernels where the lattice fills 16-row segments in two waves -- on smaller
+// lattices their fill rows per segment cost more than the launches they save
+bool use_fused(const StepParams& P) {
+    return P.adjoint_fused == 1 || (P.adjoint_fused == 0 && tail_rows(P.nx, P.ny) >= 16);
 }
 
 template <bool W, bool EXPAND>
@@ -902,6 +943,201 @@ cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double*
     const int rows = tail_rows(P.nx, P.ny);
     const dim3 g(static_cast<unsigned>((P.nx + kTileX - 1) / kTileX), static_cast<unsigned>((P.ny + rows - 1) / rows));
     k_rev_tail<W, EXPAND><<<g, kWin, kTailSmem, s>>>(P, S, lam, rows, partials);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- fused forward recomputation
+// The forward fields of P_{t-1} that the reverse step reads (moments, colour
+// fractions, Phi', grad rho^N, K, G and u) in one row wavefront, compact
+// stencil only: the same tiling as k_rev_tail, iteration k (s = y0 - 2 + k)
+// runs
+//   A (row s - 1)  gather f, colour moments, colour fractions, Phi'        (k_fwd_moments)
+//   B (row s - 2)  grad rho^N on the smaller colour fraction, n-hat       (k_fwd_normal)
+//   C (row s - 3)  K = div n-hat, G, u                                    (k_fwd_force)
+// with one barrier between stages, the stencil inputs in rings in shared
+// memory and A's gather loaded one row ahead; every owned node's fields go
+// to the planes once.  The arithmetic is that of the plane passes, term by
+// term.  (Fusing the reverse collision as a fourth stage was tried: its
+// registers left 12 warps per SM, and the four-stage kernel took 1.4x the
+// time of the passes it replaced.)
+constexpr int kHeadRows = 64;  // ring rows of shared memory, kWin floats each
+enum HeadRing : int {
+    kHChr = 0, kHChb = 4, kHRr = 8, kHRb = 12, kHJx = 16, kHJy = 20, kHGx = 24, kHGy = 28, kHNx = 32, kHNy = 36,
+    kHGfx = 40, kHGfy = 44, kHUx = 48, kHUy = 52,  // 4-row rings
+    kHPhip = 56                                    // 8-row ring
+};
+
+template <bool W>
+__global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ post, const StepParams P,
+                                                   float* __restrict__ S, const int rows) {
+    __shared__ __align__(16) float hsm[kHeadRows * kWin];
+    const int t = threadIdx.x;
+    const int nx = P.nx, ny = P.ny;
+    const size_t n = static_cast<size_t>(nx) * ny;
+    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * rows;
+    const int y_end = min(y0 + rows, ny);
+    const int xm = wrap_to(x0 - kHalo + t - 1, nx), xc = wrap_to(x0 - kHalo + t, nx), xp = wrap_to(x0 - kHalo + t + 1, nx);
+    const bool own_col = t >= kHalo && t < kWin - kHalo && x0 + t - kHalo < nx;
+    auto row_ok = [&](int r) { return !W || (r >= 0 && r < ny); };
+    auto r4 = [&](int base, int r) { return hsm + (base + (r & 3)) * kWin; };
+    auto r8 = [&](int base, int r) { return hsm + (base + (r & 7)) * kWin; };
+    // pre-collision populations of node (column xc, row y): f_i(r) = P_i(r - c_i),
+    // half-way bounce-back beyond a wall (Nbh::gather)
+    auto gather = [&](int y, float (&fr)[9], float (&fb)[9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sy = y - lcy(i);
+            size_t src;
+            int li = i;
+            if (W && (sy < 0 || sy >= ny)) {
+                li = lopp(i);
+                src = static_cast<size_t>(y) * nx + xc;
+            } else {
+                src = static_cast<size_t>(wrap_to(sy, ny)) * nx + (lcx(i) > 0 ? xm : (lcx(i) < 0 ? xp : xc));
+            }
+            fr[i] = post[static_cast<size_t>(li) * n + src];
+            fb[i] = post[static_cast<size_t>(9 + li) * n + src];
+        }
+    };
+    // compact gradient of a ring field at (row y, column t): Nbh::grad<2>
+    // (wall rows come from the mirrored ghost rows the writers add)
+    auto grad = [&](auto rowp, int y, float& gxo, float& gyo) {
+        const float* m = rowp(y);
+        const float* a = rowp(y + 1);
+        const float* b = rowp(y - 1);
+        gxo = ddx(m[t + 1], m[t - 1], a[t + 1], a[t - 1], b[t + 1], b[t - 1]);
+        gyo = ddy(a[t], b[t], a[t + 1], a[t - 1], b[t + 1], b[t - 1]);
+    };
+    auto in_A = [&](int r) { return r >= y0 - 3 && r <= y_end + 2 && row_ok(r) && t >= 1 && t < kWin - 1; };
+    auto owned = [&](int r) { return r >= y0 && r < y_end && own_col; };
+    float frn[9], fbn[9];  // next iteration's A gather
+    auto fetch = [&](int s) {
+        if (in_A(s - 1)) gather(s - 1, frn, fbn);
+    };
+    const int iters = (y_end - y0) + 5;
+    fetch(y0 - 2);
+    for (int k = 0; k < iters; ++k) {
+        const int s = y0 - 2 + k;
+        float fr[9], fb[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            fr[i] = frn[i];
+            fb[i] = fbn[i];
+        }
+        if (k + 1 < iters) fetch(s + 1);
+        // ---- A: moments at row s - 1 (k_fwd_moments)
+        {
+            const int y = s - 1;
+            if (in_A(y)) {
+                float f[9];
+                const float rr = sum9f(fr), rb = sum9f(fb);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
+                const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
+                const float inv = 1.0f / (a + b);
+                const float chr = a * inv, chb = b * inv;
+                const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
+                r4(kHChr, y)[t] = chr;
+                r4(kHChb, y)[t] = chb;
+                r8(kHPhip, y)[t] = phip;
+                r4(kHRr, y)[t] = rr;
+                r4(kHRb, y)[t] = rb;
+                r4(kHJx, y)[t] = ((f[1] + f[7]) + f[8]) - ((f[3] + f[5]) + f[4]);
+                r4(kHJy, y)[t] = ((f[1] + f[3]) + f[2]) - ((f[5] + f[7]) + f[6]);
+                if (W && (y == 0 || y == ny - 1)) {  // even mirrors beyond the walls
+                    const int g = y == 0 ? -1 : ny;
+                    r4(kHChr, g)[t] = chr;
+                    r4(kHChb, g)[t] = chb;
+                    r8(kHPhip, g)[t] = phip;
+                }
+                if (owned(y)) {
+                    const size_t o = static_cast<size_t>(y) * nx + xc;
+                    S[kRR * n + o] = rr;
+                    S[kRB * n + o] = rb;
+                    S[kCHR * n + o] = chr;
+                    S[kCHB * n + o] = chb;
+                    S[kPHIP * n + o] = phip;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- B: grad rho^N on the smaller colour fraction, n-hat at row s - 2 (k_fwd_normal)
+        {
+            const int y = s - 2;
+            if (y >= y0 - 2 && y <= y_end + 1 && row_ok(y) && t >= 2 && t < kWin - 2) {
+                const bool red_minor = r4(kHChr, y)[t] < r4(kHChb, y)[t];
+                float gx, gy;
+                if (red_minor) grad([&](int r) { return r4(kHChr, r); }, y, gx, gy);
+                else grad([&](int r) { return r4(kHChb, r); }, y, gx, gy);
+                gx *= red_minor ? 2.0f : -2.0f;
+                gy *= red_minor ? 2.0f : -2.0f;
+                float nhx, nhy;
+                normal_of(gx, gy, nhx, nhy);
+                r4(kHGx, y)[t] = gx;
+                r4(kHGy, y)[t] = gy;
+                r4(kHNx, y)[t] = nhx;
+                r4(kHNy, y)[t] = nhy;
+                if (W && (y == 0 || y == ny - 1)) {  // the normal beyond a wall: y component odd
+                    const int g = y == 0 ? -1 : ny;
+                    r4(kHNx, g)[t] = nhx;
+                    r4(kHNy, g)[t] = -nhy;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- C: curvature, force, velocity at row s - 3 (k_fwd_force)
+        {
+            const int y = s - 3;
+            if (y >= y0 - 1 && y <= y_end && row_ok(y) && t >= 3 && t < kWin - 3) {
+                float K = P.fixed_K;
+                if (P.curvature_mode == 0) {
+                    const float* nxm = r4(kHNx, y);
+                    const float* nxa = r4(kHNx, y + 1);
+                    const float* nxb = r4(kHNx, y - 1);
+                    const float* nym = r4(kHNy, y);
+                    const float* nya = r4(kHNy, y + 1);
+                    const float* nyb = r4(kHNy, y - 1);
+                    K = ddx(nxm[t + 1], nxm[t - 1], nxa[t + 1], nxa[t - 1], nxb[t + 1], nxb[t - 1]) +
+                        ddy(nya[t], nyb[t], nya[t + 1], nya[t - 1], nyb[t + 1], nyb[t - 1]);
+                }
+                const float gx = r4(kHGx, y)[t], gy = r4(kHGy, y)[t];
+                const float rr = r4(kHRr, y)[t], rb = r4(kHRb, y)[t];
+                const float rho = rr + rb;
+                const float hk = P.half_sigma * K;
+                const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
+                const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
+                const float ux = fmaf(0.5f, Gx, r4(kHJx, y)[t]) / rho;
+                const float uy = fmaf(0.5f, Gy, r4(kHJy, y)[t]) / rho;
+                r4(kHGfx, y)[t] = Gx;
+                r4(kHGfy, y)[t] = Gy;
+                r4(kHUx, y)[t] = ux;
+                r4(kHUy, y)[t] = uy;
+                if (W && (y == 0 || y == ny - 1)) {  // no-slip: u odd beyond the walls
+                    const int g = y == 0 ? -1 : ny;
+                    r4(kHUx, g)[t] = -ux;
+                    r4(kHUy, g)[t] = -uy;
+                }
+                if (owned(y)) {
+                    const size_t o = static_cast<size_t>(y) * nx + xc;
+                    S[kGX * n + o] = gx;
+                    S[kGY * n + o] = gy;
+                    S[kK * n + o] = K;
+                    S[kGFX * n + o] = Gx;
+                    S[kGFY * n + o] = Gy;
+                    S[kUX * n + o] = ux;
+                    S[kUY * n + o] = uy;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <bool W>
+cudaError_t launch_fwd_head(const float* post, const StepParams& P, float* S, cudaStream_t s) {
+    const int rows = tail_rows(P.nx, P.ny);
+    const dim3 g(static_cast<unsigned>((P.nx + kTileX - 1) / kTileX), static_cast<unsigned>((P.ny + rows - 1) / rows));
+    k_fwd_head<W><<<g, kWin, 0, s>>>(post, P, S, rows);
     return cudaGetLastError();
 }
 
@@ -1120,17 +1356,23 @@ void forward_planes(const float* post, const StepParams& P, float* S, cudaStream
     k_fwd_force<W><<<g, kAT, 0, s>>>(P, S);
 }
 
-// the reverse passes shared by both forms of one adjoint step; with the
-// compact stencil (O = 2) the passes after the collision are one fused launch
-// (k_rev_tail), which also writes lambda: `lam_out` is lambda of P_{t-1}
-// (transposed gather) or, with EXPAND, dJ/df(t) in the public layout
+// One adjoint step: `lam_out` is lambda of P_{t-1} (transposed gather) or,
+// with EXPAND, dJ/df(t) in the public layout.  With the compact stencil on a
+// large enough lattice it is three launches (k_fwd_head: the forward fields;
+// the reverse collision pass; k_rev_tail: the rest); otherwise eight plane
+// passes (seven with fixed K).
 template <int O, bool W, bool EXPAND>
 cudaError_t reverse_step(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
                          float* lam_out, cudaStream_t s) {
     const dim3 g = adj_grid(P);
+    if (O == 2 && use_fused(P)) {
+        const cudaError_t e = launch_fwd_head<W>(post, P, S, s);
+        if (e != cudaSuccess) return e;
+        k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
+        return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
+    }
     forward_planes<O, W>(post, P, S, s);
     k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
-    if (O == 2 && use_tail(P)) return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
     k_rev_force<W><<<g, kAT, 0, s>>>(P, S, partials);
     if (P.curvature_mode == 0) k_rev_normal<W><<<g, kAT, 0, s>>>(P, S);
     k_rev_moments<O, W><<<g, kAT, 0, s>>>(P, S);
@@ -1173,7 +1415,7 @@ cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* sc
 }
 
 int adj_launches_per_step(const StepParams& P) {
-    if (P.stencil_order == 2 && use_tail(P)) return 5;  // three forward passes, the collision, the fused tail
+    if (P.stencil_order == 2 && use_fused(P)) return 3;  // fused forward fields, collision pass, fused tail
     return P.curvature_mode == 0 ? 8 : 7;
 }
 

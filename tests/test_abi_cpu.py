@@ -58,7 +58,7 @@ def test_defaults_are_valid(cm):
     ("stencil_order", 4, "stencil_order"),
     ("precision", 3, "precision"),
     ("precision_reference", 2, "precision_reference"),
-    ("adjoint_tail", 3, "adjoint_tail"),
+    ("adjoint_fused", 3, "adjoint_fused"),
     ("visc_mode", 3, "visc_mode"),
     ("wall_y", 2, "wall_y"),
     ("rho0_b", 0.0, "rho0"),

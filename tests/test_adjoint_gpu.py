@@ -54,7 +54,7 @@ VJP_CASES = [
     ("rates_ghostN", dict(lambda3_r=1.5, lambda3_b=0.7, lambda6=1.2, lambda7=0.8, ghost_N_mode=1)),
     ("visc_eta_fixedK", dict(visc_mode=1, eta=0.2, curvature_mode=1, fixed_K=0.05, g_vol=(1e-4, 0.0))),
     ("ragged_walls", dict(wall_y=True, sigma=0.02, size=(131, 37))),
-    # the fused reverse tail's tiling: a lattice narrower than its 128-column
+    # the fused reverse kernels' tiling: a lattice narrower than their 128-column
     # window and shorter than a row segment; three strips of many 4-row
     # segments, so that every strip and segment seam is crossed
     ("tiny_periodic", dict(size=(5, 4))),
@@ -62,15 +62,15 @@ VJP_CASES = [
 ]
 
 
-@pytest.mark.parametrize("tail", [1, 2], ids=["fused_tail", "plane_passes"])
+@pytest.mark.parametrize("fused", [1, 2], ids=["fused_kernels", "plane_passes"])
 @pytest.mark.parametrize("name,kw", VJP_CASES)
-def test_step_vjp_matches_oracle_adjoint(name, kw, tail):
+def test_step_vjp_matches_oracle_adjoint(name, kw, fused):
     kw = dict(kw)
     nx, ny = kw.pop("size", (40, 24))
     d = I.base_params(nx, ny, sigma=kw.pop("sigma", 0.01), **kw)
     p = O.Params(**d)
     R, B = _state32(d, seed=3)
-    lat = cm.Lattice(dict(d, adjoint_tail=tail), None, None)
+    lat = cm.Lattice(dict(d, adjoint_fused=fused), None, None)
     lat.set_populations(np.stack([R, B]))
     rng = np.random.default_rng(4)
     lam_next = rng.standard_normal((2, 9, ny, nx)).astype(np.float32)
@@ -160,15 +160,15 @@ def test_adjoint_gradient_matches_oracle(wall):
 
 
 @pytest.mark.parametrize("wall", [False, True])
-def test_fused_tail_equals_plane_passes(wall):
-    """The whole checkpointed adjoint through the fused reverse tail and
-    through the four plane passes it replaces: the same objective and, up to
-    the summation order of the FP32 partial sums, the same gradients."""
+def test_fused_kernels_equal_plane_passes(wall):
+    """The whole checkpointed adjoint through the two fused reverse kernels
+    and through the eight plane passes they replace: the same objective and,
+    up to the summation order of the partial sums, the same gradients."""
     nsteps = 12
     d, rn0, u0, target = _drop_setup(96, 20.0, nsteps, g=1e-4, wall=wall)
     outs = []
-    for tail in (1, 2):
-        lat = cm.Lattice(dict(d, adjoint_tail=tail), rn0.astype(np.float32), None)
+    for fused in (1, 2):
+        lat = cm.Lattice(dict(d, adjoint_fused=fused), rn0.astype(np.float32), None)
         J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=5, want_rho_n0=True)
         outs.append((J, g, grn.double().cpu().numpy()))
         lat.close()
