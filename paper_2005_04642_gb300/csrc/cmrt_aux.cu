@@ -20,39 +20,49 @@ __device__ __forceinline__ int wrapx(int v, int n) {
 // Initial state (t = 0): at each node the equilibrium of Eq. equ_equ with
 // phi_i of Eq. eq_phi, split by colour as C_i = (rho_C / rho) f^(0)_i, from
 // rho_R = rho0_R (1 + rho^N_0)/2 and rho_B = rho0_B (1 - rho^N_0)/2 (which
-// inverts Eq. equ_rhoN_def).  Evaluated once per node in FP64 and rounded
-// once.  Each node writes its links to where the first step's pull streaming
-// will find them: f_i(r) goes to P_i(r - c_i), or to P_opp(i)(r) where
-// r - c_i lies beyond a wall (half-way bounce-back).
+// inverts Eq. equ_rhoN_def).  f^(0)_i = rho phi_i + w_i rho Q_i with the
+// velocity part Q_i = 3 c.u + 9/2 (c.u)^2 - 3/2 u^2.  The colour split and
+// rho phi_i (three link classes per node) are FP64; Q_i, small and taken
+// from FP32 velocities, is FP32 (its rounding is far below a float ulp of
+// C_i), and each C_i is one FP64 FMA rounded once to FP32.  Each node
+// writes its links to where the first step's pull streaming will find them:
+// f_i(r) goes to P_i(r - c_i), or to P_opp(i)(r) where r - c_i lies beyond a
+// wall (half-way bounce-back).
 struct InitIn {
     const float* rho_n0;
     const float* u0;
     double rho0_r, rho0_b, alpha_r, alpha_b;
 };
 
+// one thread per node: x from the block column, y from the block row (a
+// stride over rows beyond the grid's y extent)
 __global__ void k_init(InitIn in, int nx, int ny, int walls, float* __restrict__ post) {
     const size_t plane = static_cast<size_t>(nx) * ny;
-    for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < plane;
-         n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int y = static_cast<int>(n / nx);
-        const int x = static_cast<int>(n - static_cast<size_t>(y) * nx);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;  // the source columns x - c_ix
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const size_t n = static_cast<size_t>(y) * nx + x;
         const double rn = in.rho_n0 ? static_cast<double>(in.rho_n0[n]) : -1.0;
-        const double ux = in.u0 ? static_cast<double>(in.u0[n]) : 0.0;
-        const double uy = in.u0 ? static_cast<double>(in.u0[plane + n]) : 0.0;
+        const float fux = in.u0 ? in.u0[n] : 0.0f;
+        const float fuy = in.u0 ? in.u0[plane + n] : 0.0f;
         const double rr = in.rho0_r * (1.0 + rn) * 0.5;
         const double rb = in.rho0_b * (1.0 - rn) * 0.5;
         const double rho = rr + rb;
         const double inv_rho = 1.0 / rho;
         const double ar = rr * inv_rho, ab = rb * inv_rho;
-        const double phi0 = (in.alpha_r * rr + in.alpha_b * rb) * inv_rho;
-        const double phim = 1.8 * ((1.0 - in.alpha_r) * rr + (1.0 - in.alpha_b) * rb) * inv_rho;
-        const double usq = ux * ux + uy * uy;
+        // rho phi_i and w_i rho of the rest, axis and diagonal links
+        const double rphi0 = in.alpha_r * rr + in.alpha_b * rb;
+        const double rphim = 1.8 * ((1.0 - in.alpha_r) * rr + (1.0 - in.alpha_b) * rb);
+        const double rphi_c[3] = {rphi0, rphim * (1.0 / 9.0), rphim * (1.0 / 36.0)};
+        const double wrho_c[3] = {rho * (4.0 / 9.0), rho * (1.0 / 9.0), rho * (1.0 / 36.0)};
+        const float usq = fmaf(fux, fux, fuy * fuy);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double w = (i == 0) ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 36.0 : 1.0 / 9.0);
-            const double cu = lcx(i) * ux + lcy(i) * uy;
-            const double phi = (i == 0) ? phi0 : w * phim;
-            const double f0 = rho * phi + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            const int cls = i == 0 ? 0 : ((i & 1) ? 2 : 1);
+            const float cu = float(lcx(i)) * fux + float(lcy(i)) * fuy;
+            const float Q = fmaf(4.5f * cu, cu, fmaf(3.0f, cu, -1.5f * usq));
+            const double f0 = fma(wrho_c[cls], static_cast<double>(Q), rphi_c[cls]);
             const int ty = y - lcy(i);
             size_t dst;
             int li;
@@ -60,7 +70,8 @@ __global__ void k_init(InitIn in, int nx, int ny, int walls, float* __restrict__
                 dst = n;
                 li = lopp(i);
             } else {
-                dst = static_cast<size_t>(wrapx(ty, ny)) * nx + wrapx(x - lcx(i), nx);
+                const int sx = lcx(i) > 0 ? xm : (lcx(i) < 0 ? xp : x);
+                dst = static_cast<size_t>(ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty)) * nx + sx;
                 li = i;
             }
             post[li * plane + dst] = static_cast<float>(ar * f0);
@@ -190,7 +201,8 @@ dim3 flat_grid(size_t n) {
 cudaError_t launch_init_fp64(const float* rho_n0, const float* u0, int nx, int ny, int walls, double rho0_r,
                              double rho0_b, double alpha_r, double alpha_b, float* post, cudaStream_t s) {
     InitIn in{rho_n0, u0, rho0_r, rho0_b, alpha_r, alpha_b};
-    k_init<<<flat_grid(static_cast<size_t>(nx) * ny), 256, 0, s>>>(in, nx, ny, walls, post);
+    const dim3 g(static_cast<unsigned>((nx + 127) / 128), static_cast<unsigned>(ny < 65535 ? ny : 65535));
+    k_init<<<g, 128, 0, s>>>(in, nx, ny, walls, post);
     return cudaGetLastError();
 }
 
