@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define CMRT_ABI_VERSION 4
+#define CMRT_ABI_VERSION 5
 
 typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
 typedef struct cmrt_batch cmrt_batch; /* opaque, owned by the library */
