@@ -87,6 +87,7 @@ _SIGNATURES = [
 CMRT_TUNE_FORCE = 1
 
 _lib = None
+ABI_VERSION = 5  # the layout of cmrt_params and the calls this binding was written for
 
 
 def load(path: str = LIB_PATH):
@@ -102,6 +103,10 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if lib.cmrt_abi_version() != ABI_VERSION or lib.cmrt_params_size() != ctypes.sizeof(cmrt_params):
+        raise RuntimeError(f"libcmrt at {path} has ABI version {lib.cmrt_abi_version()} "
+                           f"(params {lib.cmrt_params_size()} B); this binding needs version {ABI_VERSION} "
+                           f"({ctypes.sizeof(cmrt_params)} B): rebuild it")
     _lib = lib
     return lib
 
