@@ -157,6 +157,42 @@ def test_static_drop_10k_steps_parity_bar():
     assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 1e-6
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("visc_ratio", [1.0, 10.0])
+def test_layered_full_width_10k_steps_parity_bar(visc_ratio):
+    """The layered-flow configuration at its full width (1024 x 128, walls,
+    Lambda = 100, body force 1e-6 along x, viscosity ratio 1 or 10) after 10k
+    steps, in the benchmark's launch configuration, against the oracle run on
+    a 4-column slice: the flow is invariant along x, so every one of the
+    GPU's 1024 columns must match the oracle's column at the 10k-step bar.
+
+    Colour mass: FP32 population storage alone moves it here -- the FP64
+    oracle whose state is rounded to FP32 after every step drifts by
+    2.2e-6 (red) and 3.6e-6 to 4.4e-6 (blue) over these 10k steps, because
+    the light colour's populations sit near 1e-3 and every column makes the
+    same rounding errors -- so the bar is 5e-6 here, not the 1e-6 that the
+    static drop meets."""
+    d, rn, u = I.layered_channel(nx=1024, ny=128, Lambda=100.0, visc_ratio=visc_ratio, g=1e-6)
+    ds, rns, us = I.layered_channel(nx=4, ny=128, Lambda=100.0, visc_ratio=visc_ratio, g=1e-6)
+    p, R, B = _oracle_run(ds, rns, us, 10000)
+    f = O.fields(R, B, p)
+    lat = cm.Lattice(d, rn, u)
+    d0 = lat.diagnostics()
+    lat.step(10000)
+    g = {k: v.double().cpu().numpy() for k, v in lat.fields().items()}
+    d1 = lat.diagnostics()
+    lat.close()
+    uref = max(np.abs(np.stack([f["ux"], f["uy"]])).max(), 0.01)
+    for k in ("rho_r", "rho_b", "p", "ux", "uy"):
+        ref = f[k][:, :1]  # [ny, 1]: the oracle's columns are identical
+        assert np.abs(f[k] - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0), k
+        scale = uref if k in ("ux", "uy") else np.abs(ref).max()
+        err = np.abs(g[k] - ref).max() / scale
+        assert err <= 1e-3, (k, err)
+    assert abs(d1["mass_r"] - d0["mass_r"]) / d0["mass_r"] <= 5e-6
+    assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 5e-6
+
+
 def test_diagnostics_match_oracle():
     d, rn, u = I.static_drop(n=48, radius=12.0)
     d["g_acc"] = (1e-5, -2e-5)
