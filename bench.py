@@ -362,8 +362,29 @@ def run_variants(args, cm, I, stream, fp32_ms):
                 "bytes_per_cell": nbytes, "achieved_GBs": nbytes * cells / (ms * 1e-3) / 1e9,
                 "frac_of_hbm_peak": nbytes * cells / (ms * 1e-3) / 1e9 / peak, "steps": steps,
                 "nonfinite": diag["nonfinite"]}
+        out.update(run_layered(cm, I, stream, steps, fp32_ms, peak))
         out.update(run_batch(cm, I, stream, steps, fp32_ms, peak))
         out.update(run_adjoint(cm, I, stream))
+    return out
+
+
+def run_layered(cm, I, stream, steps, fp32_ms, peak):
+    """Layered two-fluid flow (App. C): heavy fluid below a flat interface at
+    mid-height, Lambda = 100, viscosity ratio 1, walls in y, body force 1e-6
+    along x.  At 8192 x 8192 the step is bandwidth-bound like the drops
+    workload; the 1024 x 128 channel of the parity tests fills a fifth of the
+    GPU and shows the latency-bound small-lattice rate."""
+    out = {}
+    for name, nx, ny, nsteps in (("fp32_layered_8192x8192_walls_Lambda100", 8192, 8192, steps),
+                                 ("fp32_layered_1024x128_walls_Lambda100", 1024, 128, 2000)):
+        d, rn, u = I.layered_channel(nx=nx, ny=ny)
+        ms, diag = time_steps(cm, d, rn, u, nsteps, 20, stream)
+        cells = nx * ny
+        gbs = 144 * cells / (ms * 1e-3) / 1e9
+        out[name] = {"value": cells / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                     "vs_drops_8192_per_cell": (fp32_ms / (N_SIDE * N_SIDE)) / (ms / cells),
+                     "bytes_per_cell": 144, "achieved_GBs": gbs, "frac_of_hbm_peak": gbs / peak, "steps": nsteps,
+                     "nonfinite": diag["nonfinite"]}
     return out
 
 

@@ -46,6 +46,8 @@ _SIGNATURES = [
     ("cmrt_init", ctypes.c_int, [ctypes.POINTER(cmrt_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_void_p)]),
     ("cmrt_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("cmrt_set_graph_steps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("cmrt_get_graph_steps", ctypes.c_int32, [ctypes.c_void_p]),
     ("cmrt_fields", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
     ("cmrt_diagnostics", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("cmrt_get_populations", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -87,7 +89,7 @@ _SIGNATURES = [
 CMRT_TUNE_FORCE = 1
 
 _lib = None
-ABI_VERSION = 5  # the layout of cmrt_params and the calls this binding was written for
+ABI_VERSION = 6  # the layout of cmrt_params and the calls this binding was written for
 
 
 def load(path: str = LIB_PATH):
@@ -399,6 +401,14 @@ class Lattice:
 
     def step(self, n: int = 1):
         cmrt_step(self.ctx, n)
+
+    def set_graph_steps(self, steps: int):
+        """Steps per recorded CUDA graph in step() and adjoint() (0: none)."""
+        _check(load().cmrt_set_graph_steps(self.ctx, steps), self.ctx)
+
+    @property
+    def graph_steps(self):
+        return load().cmrt_get_graph_steps(self.ctx)
 
     def fields(self):
         """dict of (ny, nx) float32 CUDA tensors: rho_r, rho_b, ux, uy, p."""

@@ -60,7 +60,10 @@ struct Ctx {
         cudaGraphExec_t exec;
     };
     std::vector<AdjGraph> adj_graphs;
-    cudaStream_t adj_capture = nullptr;
+    cudaStream_t adj_capture = nullptr;  // private stream on which graphs are recorded
+    // CUDA graphs of graph_steps plain steps starting from buffer parity 0 / 1
+    int graph_steps = 32;
+    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
     size_t adj_bytes = 0;
     int rows = 128;                      // rows per CTA of the chain kernel
     int64_t t = 0;
@@ -319,6 +322,11 @@ void drop_adj_graphs(Ctx* c) {
     c->adj_graphs.clear();
 }
 
+void drop_step_graphs(Ctx* c) {
+    for (cudaGraphExec_t& g : c->step_exec)
+        if (g) cudaGraphExecDestroy(g), g = nullptr;
+}
+
 void free_all(Ctx* c) {
     if (!c->owner) {  // a member view borrows its state and flag from the batch
         for (void*& b : c->buf)
@@ -338,6 +346,7 @@ void free_all(Ctx* c) {
     c->adj_bytes = 0;
     c->adj_ckpt_cap = c->adj_seg_cap = 0;
     drop_adj_graphs(c);
+    drop_step_graphs(c);
     if (c->adj_capture) cudaStreamDestroy(c->adj_capture), c->adj_capture = nullptr;
 }
 
@@ -368,6 +377,49 @@ int step_once(Ctx* c, const void* src, void* dst, cudaError_t* err) {
         if (k_ < 0) return fail((ctx), CMRT_ECUDA, "step launch failed: %s", cudaGetErrorString(e_)); \
         (ctx)->launches += k_;                                                                       \
     } while (0)
+
+// Records graph_steps plain steps starting from buffer parity `parity` on
+// the private capture stream (the launchers enqueue on c->stream, which is
+// swapped for the recording).
+cmrt_status build_step_graph(Ctx* c, int parity) {
+    if (!c->adj_capture) CK(c, cudaStreamCreateWithFlags(&c->adj_capture, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    c->stream = c->adj_capture;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->adj_capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < c->graph_steps && e == cudaSuccess; ++k)
+            step_once(c, c->buf[(parity + k) & 1], c->buf[(parity + k + 1) & 1], &e);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c->adj_capture, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    c->stream = user;
+    if (e != cudaSuccess) return fail(c, CMRT_ECUDA, "recording the step graph failed: %s", cudaGetErrorString(e));
+    c->step_exec[parity] = exec;
+    return CMRT_OK;
+}
+
+// n plain steps on the context's stream: whole graphs of graph_steps steps
+// (an even count, so the buffer parity is unchanged), then single launches.
+cmrt_status advance(Ctx* c, int64_t n) {
+    const int per_step = c->p.stencil_order == 6 ? 4 : 1;
+    while (c->graph_steps > 0 && n >= c->graph_steps) {
+        if (!c->step_exec[c->cur] && build_step_graph(c, c->cur) != CMRT_OK) return CMRT_ECUDA;
+        CK(c, cudaGraphLaunch(c->step_exec[c->cur], c->stream));
+        c->t += c->graph_steps;
+        c->launches += static_cast<int64_t>(c->graph_steps) * per_step;
+        n -= c->graph_steps;
+    }
+    for (; n > 0; --n) {
+        STEP(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+        c->cur ^= 1;
+        c->t++;
+    }
+    return CMRT_OK;
+}
 
 // Writes the state at t = 0 into c->buf[c->cur] (Eqs. equ_rhoN_def, equ_equ):
 // the equilibrium of the colour field rho_n0 and velocity u0 (host or device
@@ -530,17 +582,32 @@ cmrt_status cmrt_step(cmrt_ctx* h, int64_t n) {
     if (n < 0) return fail(c, CMRT_EINVAL, "n must be >= 0");
     if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
-    for (int64_t k = 0; k < n; ++k) {
-        STEP(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
-        c->cur ^= 1;
-        c->t++;
-        if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0) {
-            cmrt_status st = check_flag(c);
-            if (st != CMRT_OK) return st;
-        }
+    int64_t left = n;
+    while (left > 0) {
+        // up to the next non-finite check
+        int64_t chunk = left;
+        if (c->p.diag_every > 0) chunk = std::min<int64_t>(chunk, c->p.diag_every - c->t % c->p.diag_every);
+        left -= chunk;
+        cmrt_status st = advance(c, chunk);
+        if (st != CMRT_OK) return st;
+        if (c->p.diag_every > 0 && (c->t % c->p.diag_every) == 0 && (st = check_flag(c)) != CMRT_OK) return st;
     }
     return CMRT_OK;
 }
+
+cmrt_status cmrt_set_graph_steps(cmrt_ctx* h, int32_t steps) {
+    Ctx* c = live(h);
+    if (!c) return CMRT_ESTATE;
+    if (steps < 0 || steps % 2 != 0) return fail(c, CMRT_EINVAL, "graph steps must be 0 or a positive even number");
+    if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);
+    if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_step_graphs(c);
+    c->graph_steps = steps;
+    return CMRT_OK;
+}
+
+int32_t cmrt_get_graph_steps(const cmrt_ctx* h) { return h ? h->c.graph_steps : -1; }
 
 cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, float* uy, float* p) {
     Ctx* c = live(h);
@@ -1558,13 +1625,12 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if ((st = adj_zero(c)) != CMRT_OK) return st;
     // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
     CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
-    for (int64_t t = 0; t < nsteps; ++t) {
-        STEP(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
-        c->cur ^= 1;
-        c->t++;
-        if ((t + 1) % K == 0 && t + 1 < nsteps)
-            CK(c, cudaMemcpyAsync(c->adj_ckpt + static_cast<size_t>((t + 1) / K) * n18, c->buf[c->cur], state,
-                                  cudaMemcpyDeviceToDevice, c->stream));
+    for (size_t k = 1; k <= nck; ++k) {
+        if ((st = advance(c, std::min<int64_t>(static_cast<int64_t>(k) * K, nsteps) - static_cast<int64_t>(k - 1) * K)) !=
+            CMRT_OK)
+            return st;
+        if (k < nck)
+            CK(c, cudaMemcpyAsync(c->adj_ckpt + k * n18, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
     }
     // objective and its adjoint
     int a = 0;

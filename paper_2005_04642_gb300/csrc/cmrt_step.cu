@@ -709,17 +709,28 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
     }
 }
 
+// A tile of rows [y0, y0 + rows) touches population rows y0 - 4 .. y0 + rows + 3
+// and runs its stages on rows y0 - 3 .. y0 + rows + 2.  When all of these lie
+// inside [1, ny - 2] no wall condition can apply (no bounce-back link, no
+// mirrored row is written or read), and the periodic form of the pipeline
+// computes exactly the same values with fewer instructions.
+__device__ __forceinline__ bool away_from_walls(int y0, int rows, int ny) { return y0 >= 5 && y0 + rows + 5 <= ny; }
+
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 __global__ void __launch_bounds__(pass_threads(MODE), pass_ctas_per_sm<L>(MODE))
     k_chain(const char* __restrict__ src, char* __restrict__ dst, const StepParams P, const int rows, FieldOut fo,
             unsigned* __restrict__ flag, double* __restrict__ partials) {
     extern __shared__ __align__(16) char smem[];
-    const Rings<L, WALLS> R = make_rings<L, WALLS>(smem, P.ny);
     const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
 
     DiagAcc acc;
-    chain_tile<L, VEC, WALLS, MODE, PRE>(R, pop_addr, src, dst, P, static_cast<int>(blockIdx.x) * kTileX,
-                                         static_cast<int>(blockIdx.y) * rows, rows, fo, flag, acc);
+    const int x0 = static_cast<int>(blockIdx.x) * kTileX, y0 = static_cast<int>(blockIdx.y) * rows;
+    if (WALLS && away_from_walls(y0, rows, P.ny))
+        chain_tile<L, VEC, false, MODE, PRE>(make_rings<L, false>(smem, P.ny), pop_addr, src, dst, P, x0, y0, rows, fo,
+                                             flag, acc);
+    else
+        chain_tile<L, VEC, WALLS, MODE, PRE>(make_rings<L, WALLS>(smem, P.ny), pop_addr, src, dst, P, x0, y0, rows, fo,
+                                             flag, acc);
     const int t = threadIdx.x;
 
     if (MODE == Pass::Diag) {
@@ -774,7 +785,7 @@ __global__ void __launch_bounds__(kStepThreads, pass_ctas_per_sm<L>(Pass::Step))
         const StepParams P = A.params[w.member];  // a register copy: stores cannot alias it
         const size_t off = A.offsets[w.member];
         DiagAcc acc;
-        if (P.wall_y)
+        if (P.wall_y && !away_from_walls(w.y0, w.rows, P.ny))
             chain_tile<L, VEC, true, Pass::Step, false>(make_rings<L, true>(smem, P.ny), pop_addr, A.src + off, A.dst + off, P, w.x0, w.y0, w.rows,
                                                         FieldOut{}, A.flags + w.member, acc);
         else
@@ -902,14 +913,15 @@ dim3 chain_grid(int nx, int ny, int rows) {
 int chain_rows(int nx, int ny, int sms, int precision) {
     // Rows per CTA: each CTA spends (rows + 8) row-iterations (8 fill the
     // pipeline), and the CTAs run in waves of (SMs x resident CTAs); pick
-    // the segment length that minimises waves x (rows + 8).
+    // the segment length that minimises waves x (rows + 8).  Short segments
+    // (1, 2, 4 rows) win on lattices too small to fill one wave.
     const int strips = (nx + kTileX - 1) / kTileX;
     const int per_sm = precision == kPrecF32 ? pass_ctas_per_sm<LayoutF32>(Pass::Step)
                                              : pass_ctas_per_sm<LayoutF16>(Pass::Step);
     const long slots = static_cast<long>(per_sm) * (sms > 0 ? sms : 1);
     int best = 8;
     long best_cost = -1;
-    for (int rows = 8; rows <= 512; rows += 8) {
+    for (int rows = 1; rows <= 512; rows = rows < 8 ? 2 * rows : rows + 8) {
         const long segs = (ny + rows - 1) / rows;
         const long waves = (strips * segs + slots - 1) / slots;
         const long cost = waves * (rows + 8);
