@@ -27,8 +27,11 @@
  * - x is periodic.  y is periodic (wall_y = 0) or bounded by half-way
  *   bounce-back walls at y = -1/2 and y = ny - 1/2 (wall_y = 1).
  * - Every pointer argument may point to host memory or to device memory of
- *   the context's device; the library detects which (cudaPointerGetAttributes)
- *   and copies through its own staging buffer when it is host memory.  The
+ *   the context's device; the library detects which (cudaPointerGetAttributes).
+ *   Page-locked host memory mapped for the device is read and written by the
+ *   kernels in place; other host memory is copied through the state buffer
+ *   that does not hold the current state (dead between steps) or, where that
+ *   is too small, through the library's own staging buffer.  The
  *   caller owns every buffer it passes; the library owns everything it
  *   allocates and frees it in cmrt_destroy.
  * - Calls are asynchronous on the context's stream unless stated; a call

@@ -269,6 +269,21 @@ bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device-side address of page-locked host memory (cudaHostAlloc,
+// cudaHostRegister) mapped for the context's device, or null for any other
+// memory.  Kernels read and write such memory directly over the host link
+// (NVLink-C2C on Grace), which needs no staging buffer and no copy-engine
+// transfer.
+void* mapped_host(const Ctx* c, const void* ptr) {
+    if (!ptr) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer && a.device == c->device) ? a.devicePointer : nullptr;
+}
+
 cmrt_status ensure_staging(Ctx* c, size_t bytes) {
     Staging& st = *c->stg;
     if (st.bytes >= bytes) return CMRT_OK;
@@ -378,6 +393,17 @@ int step_once(Ctx* c, const void* src, void* dst, cudaError_t* err) {
         (ctx)->launches += k_;                                                                       \
     } while (0)
 
+// The state buffer that does not hold the current state.  Between steps it
+// is dead (the next step overwrites all of it), so a call that moves data
+// between host memory and the device stages through its first `floats`
+// floats instead of allocating: nothing is allocated on the device after
+// cmrt_init for host inputs of an FP32 state or for host outputs of
+// cmrt_fields.  Null when the buffer is smaller than that.
+float* idle_buffer(Ctx* c, size_t floats) {
+    const size_t have = cells(*c) * cmrt::state_node_bytes(c->p.precision);
+    return floats * sizeof(float) <= have ? static_cast<float*>(c->buf[c->cur ^ 1]) : nullptr;
+}
+
 // Records graph_steps plain steps starting from buffer parity `parity` on
 // the private capture stream (the launchers enqueue on c->stream, which is
 // swapped for the recording).
@@ -427,25 +453,29 @@ cmrt_status advance(Ctx* c, int64_t n) {
 cmrt_status init_state(Ctx* c, const float* rho_n0, const float* u0) {
     const cmrt_params* p = &c->p;
     const size_t n = cells(*c);
-    // inputs: copy host arrays into staging (after an FP32 state area when the
-    // state is stored in 16 bits and has to be encoded from FP32)
+    // inputs: device memory and mapped page-locked host memory are read by
+    // the kernel in place; other host memory is copied into the idle state
+    // buffer (FP32 storage) or into staging after an FP32 state area (16-bit
+    // storage, encoded from FP32)
     const float* d_rn = rho_n0;
     const float* d_u = u0;
     const bool rn_host = rho_n0 && !is_device_ptr(rho_n0);
     const bool u_host = u0 && !is_device_ptr(u0);
+    if (rn_host) d_rn = static_cast<const float*>(mapped_host(c, rho_n0));
+    if (u_host) d_u = static_cast<const float*>(mapped_host(c, u0));
+    const bool rn_copy = rn_host && !d_rn, u_copy = u_host && !d_u;
     const bool packed = p->precision != 0;
-    const size_t in_off = packed ? 18 * n : 0;
-    if (rn_host || u_host || packed) {
-        if (ensure_staging(c, (in_off + ((rn_host || u_host) ? 3 * n : 0)) * sizeof(float)) != CMRT_OK)
-            return CMRT_ENOMEM;
-        if (rn_host) {
-            CK(c, cudaMemcpyAsync(c->stg->ptr + in_off, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-            d_rn = c->stg->ptr + in_off;
+    const size_t need = packed ? 18 * n + ((rn_copy || u_copy) ? 3 * n : 0) : 0;
+    if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+    if (rn_copy || u_copy) {
+        float* in = packed ? c->stg->ptr + 18 * n : idle_buffer(c, 3 * n);
+        if (rn_copy) {
+            CK(c, cudaMemcpyAsync(in, rho_n0, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            d_rn = in;
         }
-        if (u_host) {
-            CK(c, cudaMemcpyAsync(c->stg->ptr + in_off + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice,
-                                  c->stream));
-            d_u = c->stg->ptr + in_off + n;
+        if (u_copy) {
+            CK(c, cudaMemcpyAsync(in + n, u0, 2 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            d_u = in + n;
         }
     }
     float* post32 = packed ? c->stg->ptr : static_cast<float*>(c->buf[c->cur]);
@@ -617,11 +647,27 @@ cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, floa
     float* outs[5] = {rho_r, rho_b, ux, uy, p};
     float* dev[5];
     bool any_host = false;
-    for (int k = 0; k < 5; ++k) any_host |= (outs[k] && !is_device_ptr(outs[k]));
-    if (any_host && ensure_staging(c, 5 * n * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+    // device memory and mapped page-locked host memory are written by the
+    // kernel in place; other host outputs go to the idle state buffer (5 of
+    // its 11 or 18 floats per node) and are copied out
+    bool copy[5] = {false, false, false, false, false};
     for (int k = 0; k < 5; ++k) {
-        if (!outs[k]) dev[k] = nullptr;
-        else dev[k] = is_device_ptr(outs[k]) ? outs[k] : c->stg->ptr + k * n;
+        dev[k] = outs[k];
+        if (outs[k] && !is_device_ptr(outs[k])) {
+            dev[k] = static_cast<float*>(mapped_host(c, outs[k]));
+            copy[k] = !dev[k];
+            any_host = true;
+        }
+    }
+    float* scratch = nullptr;
+    if (copy[0] || copy[1] || copy[2] || copy[3] || copy[4]) {
+        scratch = idle_buffer(c, 5 * n);
+        if (!scratch) {
+            if (ensure_staging(c, 5 * n * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
+            scratch = c->stg->ptr;
+        }
+        for (int k = 0; k < 5; ++k)
+            if (copy[k]) dev[k] = scratch + k * n;
     }
     const cmrt::FieldOut fo{dev[0], dev[1], dev[2], dev[3], dev[4]};
     if (c->p.stencil_order == 6) {
@@ -634,8 +680,7 @@ cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, floa
     }
     if (any_host) {
         for (int k = 0; k < 5; ++k)
-            if (outs[k] && dev[k] != outs[k])
-                CK(c, cudaMemcpyAsync(outs[k], dev[k], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+            if (copy[k]) CK(c, cudaMemcpyAsync(outs[k], dev[k], n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
     return CMRT_OK;
@@ -677,9 +722,12 @@ cmrt_status cmrt_get_populations(cmrt_ctx* h, float* dst) {
     const size_t n18 = cells(*c) * 18;
     const size_t bytes = n18 * sizeof(float);
     const bool host = !is_device_ptr(dst);
+    float* mapped = host ? static_cast<float*>(mapped_host(c, dst)) : nullptr;
+    const bool copy = host && !mapped;
     const bool packed = c->p.precision != 0;
-    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (host dst)]
-    const size_t need = (packed ? n18 : 0) + (host ? n18 : 0);
+    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (unmapped host dst)];
+    // an FP32 state copies out through the idle state buffer instead
+    const size_t need = packed ? n18 + (copy ? n18 : 0) : 0;
     if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
     const float* post32 = static_cast<const float*>(c->buf[c->cur]);
     if (packed) {
@@ -687,13 +735,11 @@ cmrt_status cmrt_get_populations(cmrt_ctx* h, float* dst) {
         c->launches++;
         post32 = c->stg->ptr;
     }
-    float* d = host ? c->stg->ptr + (packed ? n18 : 0) : dst;
+    float* d = copy ? (packed ? c->stg->ptr + n18 : idle_buffer(c, n18)) : (mapped ? mapped : dst);
     CK(c, cmrt::launch_stream_out(post32, c->sp, d, c->stream));
     c->launches++;
-    if (host) {
-        CK(c, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
-    }
+    if (copy) CK(c, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (host) CK(c, cudaStreamSynchronize(c->stream));
     return CMRT_OK;
 }
 
@@ -706,12 +752,16 @@ cmrt_status cmrt_set_populations(cmrt_ctx* h, const float* src) {
     const size_t bytes = n18 * sizeof(float);
     const float* s = src;
     const bool host = !is_device_ptr(src);
+    const float* mapped = host ? static_cast<const float*>(mapped_host(c, src)) : nullptr;
+    const bool copy = host && !mapped;
     const bool packed = c->p.precision != 0;
-    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (host src)]
-    const size_t need = (packed ? n18 : 0) + (host ? n18 : 0);
+    // staging: [FP32 post-collision planes (16-bit storage)] [pre-collision copy (unmapped host src)];
+    // an FP32 state copies in through the idle state buffer instead
+    const size_t need = packed ? n18 + (copy ? n18 : 0) : 0;
     if (need && ensure_staging(c, need * sizeof(float)) != CMRT_OK) return CMRT_ENOMEM;
-    if (host) {
-        float* hs = c->stg->ptr + (packed ? n18 : 0);
+    if (mapped) s = mapped;
+    if (copy) {
+        float* hs = packed ? c->stg->ptr + n18 : idle_buffer(c, n18);
         CK(c, cudaMemcpyAsync(hs, src, bytes, cudaMemcpyHostToDevice, c->stream));
         s = hs;
     }
