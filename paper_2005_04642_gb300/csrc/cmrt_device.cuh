@@ -10,6 +10,17 @@
 
 namespace cmrt {
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be
+// scheduled while the kernel before it on the stream is still finishing;
+// pdl_begin, its first statement, waits until that kernel has completed and
+// its writes are visible, before this kernel touches global memory, and then
+// lets the next kernel be scheduled likewise (one kernel ahead at most).  For
+// a kernel launched without the attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // D2Q9 links (Sec. 3, Fig. 1 caption: odd i are the longer links; App. A
 // weights w_0 = 4/9, w_odd = 1/36, w_even = 1/9).  Link i = 1..8 runs

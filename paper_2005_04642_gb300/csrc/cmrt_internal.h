@@ -6,7 +6,33 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace cmrt {
+
+// Launches `kernel` with programmatic stream serialisation: the launch may
+// overlap the tail of the previous kernel on the stream, which removes the
+// gap between back-to-back kernels on small lattices.  Every kernel launched
+// this way starts with pdl_begin() (cmrt_device.cuh).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // the arguments, converted to the kernel's parameter types, by address
+    return [&](std::remove_cv_t<std::remove_reference_t<KArgs>>... a) {
+        void* ptrs[] = {static_cast<void*>(&a)...};
+        return cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(kernel), ptrs);
+    }(static_cast<Args&&>(args)...);
+}
 
 // Parameters of one step in the form the kernels use: FP32 coefficients
 // derived once on the host (in FP64) from cmrt_params.

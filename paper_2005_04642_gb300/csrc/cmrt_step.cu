@@ -720,6 +720,7 @@ template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 __global__ void __launch_bounds__(pass_threads(MODE), pass_ctas_per_sm<L>(MODE))
     k_chain(const char* __restrict__ src, char* __restrict__ dst, const StepParams P, const int rows, FieldOut fo,
             unsigned* __restrict__ flag, double* __restrict__ partials) {
+    pdl_begin();
     extern __shared__ __align__(16) char smem[];
     const unsigned pop_addr = static_cast<unsigned>(__cvta_generic_to_shared(smem));
 
@@ -826,6 +827,7 @@ cudaError_t batch_launch(const BatchArgs& A, int grid, cudaStream_t s) {
 }
 
 __global__ void k_diag_reduce(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    pdl_begin();
     __shared__ double red[kThreads / 32][kDiagSlots];
     double v[kDiagSlots] = {0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -874,9 +876,8 @@ cudaError_t launch_one(const void* src, void* dst, const StepParams& P, int rows
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    k_chain<L, VEC, WALLS, MODE, PRE><<<chain_grid(P.nx, P.ny, rows), pass_threads(MODE), smem, s>>>(
-        static_cast<const char*>(src), static_cast<char*>(dst), P, rows, fo, flag, partials);
-    return cudaGetLastError();
+    return launch_pdl(k_chain<L, VEC, WALLS, MODE, PRE>, chain_grid(P.nx, P.ny, rows), dim3(pass_threads(MODE)), smem,
+                      s, static_cast<const char*>(src), static_cast<char*>(dst), P, rows, fo, flag, partials);
 }
 
 template <class L, Pass MODE, bool PRE = false>
@@ -952,8 +953,7 @@ cudaError_t launch_diag_partials_pre(const float* pre, const StepParams& P, int 
 }
 
 cudaError_t launch_diag_reduce(const double* partials, int nblocks, double* out, cudaStream_t s) {
-    k_diag_reduce<<<1, kThreads, 0, s>>>(partials, nblocks, out);
-    return cudaGetLastError();
+    return launch_pdl(k_diag_reduce, dim3(1), dim3(kThreads), 0, s, partials, nblocks, out);
 }
 
 cudaError_t prepare_batch(int precision, bool vec, int* ctas_per_sm) {
