@@ -70,9 +70,10 @@ struct FieldOut {
     float* p;
 };
 
-// Geometry of the fused row-marching kernel: a CTA of kThreads threads owns a
-// strip of kTileX columns (plus a 4-column halo on each side, kWin columns in
-// all) and marches down kRows rows of it.
+// Geometry of the fused row-marching kernel: a CTA owns a strip of kTileX
+// columns (plus a 4-column halo on each side, kWin columns in all) and marches
+// down a segment of rows of it (chain_rows); each of its thread groups has
+// kThreads threads, one per window column.
 constexpr int kThreads = 128;
 constexpr int kWin = 128;
 constexpr int kHalo = 4;

@@ -15,12 +15,12 @@
 // the other buffer at the node itself, so every HBM access is coalesced:
 // 72 B (FP32) or 44 B (16-bit) read and as much written per node.
 //
-// A CTA of 128 threads owns a strip of 120 columns (plus 4 halo columns on
-// each side, 128 in all: one thread per column) and marches down a segment
-// of rows.  Rows of the state stream into an 8-row ring in shared memory
-// with 16-byte cp.async copies, two rows ahead of use.  Each iteration runs
-// a wavefront of four stages on consecutive rows, each stage reading only
-// what the previous one left in shared memory:
+// A CTA owns a strip of 120 columns (plus 4 halo columns on each side, 128
+// in all: one thread per column in each of its thread groups) and marches
+// down a segment of rows.  Rows of the state stream into a 9-row ring in
+// shared memory with 16-byte cp.async copies, two rows ahead of use.  Each
+// iteration runs a wavefront of four stages on consecutive rows, each stage
+// reading only what the previous one left in shared memory:
 //   A (row s-1)  gather f, colour moments, red fraction, Phi'  (tile + 3)
 //   B (row s-2)  grad rho^N and n-hat with the compact stencil   (tile + 2)
 //   C (row s-3)  K = div n-hat, force G, force-adjusted u        (tile + 1)
@@ -53,13 +53,15 @@ constexpr int kBFloats = (4 * 2 + 5 * 2) * kWin;  // grad rho^N, n-hat
 constexpr int kCFloats = (4 * 2 + 5 * 2) * kWin;  // G, u
 
 // The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
-// kThreads ("front") stream the rows in and run stages A-C, while the other
-// kThreads ("back") run stage D one row iteration behind them.
+// kThreads ("front") stream the rows in and run stages A-B, while the other
+// kThreads ("back") run stages C-D one row iteration behind them.
 constexpr int kStepThreads = 2 * kThreads;
 // Named barriers (0 is __syncthreads): the front among themselves; front ->
-// back "stage C of iteration k is in shared memory" and back -> front "stage
-// D of iteration k is done with its rows", each alternating between two ids
-// by the parity of k so that no barrier sees arrivals of two iterations.
+// back "stages A and B of iteration k are in shared memory" (kBarC, the
+// hand-off to stage C) and back -> front "stages C and D of iteration k are
+// done with their rows" (kBarD), each alternating between two ids by the
+// parity of k so that no barrier sees arrivals of two iterations; the back
+// among themselves between C and D.
 constexpr int kBarFront = 1;
 constexpr int kBarC = 2;  // 2, 3
 constexpr int kBarD = 4;  // 4, 5
