@@ -223,7 +223,7 @@ def lambda3_field(rho_n, rho, p: Params):
 
 
 # ---------------------------------------------------------------------------
-# Finite differences (Sec. 2 "compact second order stencils"; App. B)
+# Finite differences (the compact second-order stencils of Sec. 2; App. B)
 # ---------------------------------------------------------------------------
 def value_at_offset(field_, dx, dy, p: Params, parity=1):
     """field(r + (dx, dy)) on the lattice.
