@@ -547,7 +547,7 @@ def collide_and_recolour(R, B, p: Params, d: Derived = None):
 
 def step(R, B, p: Params):
     """One time step t -> t + 1: collide, recolour, stream (Eq. equ_evolution;
-    Sec. 3 "colour is finally re-allocated")."""
+    Sec. 3 puts the recolouring last, after the collision)."""
     Rpp, Bpp = collide_and_recolour(R, B, p)
     return stream(Rpp, p), stream(Bpp, p)
 
