@@ -486,6 +486,48 @@ def run_batch(cm, I, stream, steps, fp32_ms, peak):
     return res
 
 
+def run_adjoint_only(args):
+    """Only the discrete adjoint (cmrt_adjoint) on the drops field of
+    args.side (16 drops per 2048^2, gravity 1e-5 along -y): args.steps steps
+    with checkpoints every args.ckpt_every, against as many forward steps.
+    A short run for kernel launch lists of the reverse passes."""
+    import torch
+
+    from paper_2005_04642_gb300 import cmrt as cm
+    from paper_2005_04642_gb300 import inputs as I
+    n, T, K = args.side, args.steps, args.ckpt_every
+    ndrops = max(1, round(16 * (n / 2048.0) ** 2))
+    d, rn0, _ = I.random_drops(n, n, ndrops, 8.0, 64.0, 3, Lambda=10.0, g_acc=(0.0, -1e-5))
+    rn = torch.from_numpy(rn0.astype(np.float32)).cuda()
+    stream = torch.cuda.current_stream()
+    lt = cm.Lattice(dict(d, sigma=1.05 * d["sigma"]), rn, None, stream=stream)
+    lt.step(T)
+    f = lt.fields()
+    a, b = f["rho_r"] / d["rho0_r"], f["rho_b"] / d["rho0_b"]
+    target = ((a - b) / (a + b)).contiguous()
+    lt.close()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = cm.Lattice(d, rn, None, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(T)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / T
+    lat.close()
+    lat = cm.Lattice(d, rn, None, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J, g, _ = lat.adjoint(T, target, ckpt_every=K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj = e0.elapsed_time(e1) / T
+    lat.close()
+    print(json.dumps({"adjoint_only": True, "side": n, "drops": ndrops, "steps": T, "ckpt_every": K,
+                      "forward_ms_per_step": fwd, "adjoint_ms_per_step": adj, "adjoint_vs_forward": adj / fwd,
+                      "J": J}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -497,7 +539,14 @@ def main():
                     help="skip the reduced-precision timings reported under 'variants'")
     ap.add_argument("--side", type=int, default=N_SIDE,
                     help="lattice side; smaller sides (same drop density) are for profiling captures")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only cmrt_adjoint on the drops field of --side (--steps steps, checkpoints every "
+                         "--ckpt-every); a short run for launch lists of the reverse passes")
+    ap.add_argument("--ckpt-every", type=int, default=10)
     args = ap.parse_args()
+    if args.adjoint_only:
+        run_adjoint_only(args)
+        return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
