@@ -52,6 +52,9 @@
 extern "C" {
 #endif
 
+/* Raised whenever cmrt_params changes layout or a call is added or changes
+ * meaning; bindings check it (cmrt_abi_version) before use.  6: per-context
+ * step graphs (cmrt_set_graph_steps, cmrt_get_graph_steps). */
 #define CMRT_ABI_VERSION 6
 
 typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
