@@ -93,6 +93,46 @@ def test_steps_match_oracle_elementwise(name, nx, ny, wall, extra):
     assert err < 2e-6, err
 
 
+# ---------------------------------------------------------------- degenerate fields
+@pytest.mark.parametrize("rn_value,wall,g", [(-1.0, True, 1e-5), (1.0, True, 1e-5), (0.0, False, 0.0)],
+                         ids=["pure_blue_channel", "pure_red_channel", "uniform_mixture"])
+def test_uniform_colour_fields(rn_value, wall, g):
+    """A single-colour channel (rho^N = -1 or +1 everywhere, body force along
+    x between walls) is one-fluid flow: grad rho^N, n-hat and the recolour
+    flux vanish, so the absent colour stays exactly zero; a uniform 50/50
+    mixture at rest stays uniform.  Both match the oracle element by element."""
+    nx, ny = 24, 20
+    d = I.base_params(nx, ny, wall_y=wall, g_acc=(g, 0.0))
+    rn = np.full((ny, nx), rn_value)
+    u = np.zeros((2, ny, nx))
+    p, R, B = _oracle_run(d, rn, u, 60)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(60)
+    pops = lat.populations()
+    assert _pop_err(lat, R, B) < 2e-6
+    if rn_value == -1.0:
+        assert float(pops[0].abs().max()) == 0.0  # no red appears
+    if rn_value == 1.0:
+        assert float(pops[1].abs().max()) == 0.0  # no blue appears
+    if rn_value == 0.0:
+        ref = pops[:, :, :1, :1].expand_as(pops)
+        assert torch.equal(pops, ref)  # every node keeps the same populations
+    lat.close()
+
+
+def test_equal_densities_match_oracle():
+    """Lambda = 1 (both colours of density 1, alpha = 1/2 for both): the
+    density-contrast terms vanish; a drop under a force still matches."""
+    d = I.base_params(32, 28, rho0_r=1.0, rho0_b=1.0, g_acc=(1e-5, -2e-5), wall_y=True, sigma=0.01)
+    rn = I.drops_field(32, 28, [(16.0, 14.0)], [7.0], periodic_y=False)
+    u = I.velocity_noise(32, 28, 1e-4, 7)
+    p, R, B = _oracle_run(d, rn, u, 20)
+    lat = cm.Lattice(d, rn, u)
+    lat.step(20)
+    assert _pop_err(lat, R, B) < 2e-6
+    lat.close()
+
+
 def test_set_then_step_matches_oracle():
     nx, ny = 96, 70
     d = I.base_params(nx, ny, rho0_r=1.0, rho0_b=0.01, alpha_light=0.5)
