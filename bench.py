@@ -435,12 +435,15 @@ def run_adjoint(cm, I, stream):
     256^2 drop of radius 32 (Lambda 10, gravity 1e-5 along -y) over 4000 steps
     with checkpoints every 200, and a 2048^2 lattice of the same drops field
     over 200 steps (checkpoints every 20) where launch latency no longer
-    dominates.  The objective's target is the final colour field of a run
-    with sigma 5 % larger."""
+    dominates; each also with every state kept (ckpt_every = 1: 19 GB and
+    60 GB of HBM, no recomputation).  The objective's target is the final
+    colour field of a run with sigma 5 % larger."""
     import torch
     res = {}
     for name, n, nsteps, K, drops in (("adjoint_256x256_drop_4000steps", 256, 4000, 200, 1),
-                                      ("adjoint_2048x2048_drops_200steps", 2048, 200, 20, 16)):
+                                      ("adjoint_256x256_drop_4000steps_every_state_kept", 256, 4000, 1, 1),
+                                      ("adjoint_2048x2048_drops_200steps", 2048, 200, 20, 16),
+                                      ("adjoint_2048x2048_drops_200steps_every_state_kept", 2048, 200, 1, 16)):
         if drops == 1:
             d = I.base_params(n, n, rho0_r=1.0, rho0_b=0.1, g_acc=(0.0, -1e-5))
             rn0 = I.drops_field(n, n, [(n / 2.0, n / 2.0)], [32.0], dtype=np.float32)

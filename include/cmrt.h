@@ -250,7 +250,9 @@ cmrt_status cmrt_step_vjp(cmrt_ctx* c, const float* lam_next, float* lam, double
  * t0 the current time.  Runs the nsteps forward steps (the context ends at
  * t0 + nsteps, as after cmrt_step), keeping a checkpoint every ckpt_every
  * steps, then sweeps the segments backwards, recomputing each from its
- * checkpoint.  Device memory: (ceil(nsteps/ckpt_every) + ckpt_every + 1)
+ * checkpoint.  ckpt_every = 1 keeps every state, written in place by the
+ * forward steps, and recomputes nothing: the cheapest sweep where HBM holds
+ * nsteps states.  Device memory: (ceil(nsteps/ckpt_every) + ckpt_every + 1)
  * states of 72 B per node plus 38 scratch planes, kept for later calls.
  * target:  float[ny][nx] (host or device).
  * J:       NULL or receives J (FP64 sum).

@@ -1675,7 +1675,20 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if ((st = adj_zero(c)) != CMRT_OK) return st;
     // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
     CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
-    for (size_t k = 1; k <= nck; ++k) {
+    if (K == 1) {
+        // every state is kept (memory permitting, the cheapest sweep): step t
+        // reads slot t of the checkpoint array and writes slot t + 1 (the last
+        // step the lattice's other buffer), so that the reverse sweep reads
+        // each state in place -- no copies and no recomputation
+        for (int64_t t = 0; t < nsteps; ++t) {
+            void* dst = t + 1 < nsteps ? static_cast<void*>(c->adj_ckpt + static_cast<size_t>(t + 1) * n18)
+                                       : c->buf[c->cur ^ 1];
+            STEP(c, c->adj_ckpt + static_cast<size_t>(t) * n18, dst);
+            c->t++;
+        }
+        c->cur ^= 1;
+    }
+    for (size_t k = 1; K > 1 && k <= nck; ++k) {
         if ((st = advance(c, std::min<int64_t>(static_cast<int64_t>(k) * K, nsteps) - static_cast<int64_t>(k - 1) * K)) !=
             CMRT_OK)
             return st;
@@ -1687,11 +1700,18 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     CK(c, cmrt::launch_adjoint_seed(static_cast<const float*>(c->buf[c->cur]), d_target, c->sp, c->adj_scratch,
                                     c->adj_partials, c->adj_lam[a], c->stream));
     c->launches += 2;
-    // segments in reverse: the checkpoint goes to slot 0 of the segment
-    // buffer, then one graph recomputes the segment's states from it and runs
-    // its reverse steps
+    // reverse sweep.  K = 1: each reverse step reads its kept state.
+    // Otherwise segments in reverse: the checkpoint goes to slot 0 of the
+    // segment buffer, then one graph recomputes the segment's states from it
+    // and runs its reverse steps
     const int per_step = c->p.stencil_order == 6 ? 4 : 1;
-    for (int64_t k = static_cast<int64_t>(nck) - 1; k >= 0; --k) {
+    if (K == 1) {
+        for (int64_t t = nsteps - 1; t >= 0; --t, a ^= 1)
+            CK(c, cmrt::launch_adjoint_step(c->adj_ckpt + static_cast<size_t>(t) * n18, c->adj_lam[a], c->sp,
+                                            c->adj_scratch, c->adj_partials, c->adj_lam[a ^ 1], c->stream));
+        c->launches += nsteps * cmrt::adj_launches_per_step(c->sp);
+    }
+    for (int64_t k = static_cast<int64_t>(nck) - 1; K > 1 && k >= 0; --k) {
         const int64_t len = std::min((k + 1) * K, nsteps) - k * K;
         CK(c, cudaMemcpyAsync(c->adj_seg, c->adj_ckpt + static_cast<size_t>(k) * n18, state, cudaMemcpyDeviceToDevice,
                               c->stream));
