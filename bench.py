@@ -480,8 +480,15 @@ def run_adjoint(cm, I, stream):
         dev_bytes = cm.cmrt_device_bytes(lat.ctx)
         lat.close()
         torch.cuda.empty_cache()
-        res[name] = {"forward_ms_per_step": t_fwd / nsteps, "adjoint_ms_per_step": t_adj / nsteps,
+        # one reverse step against one forward step: the call minus its forward
+        # run and its segment replay (nsteps - ceil(nsteps / K) recomputed steps,
+        # the same kernel as the forward steps), per step
+        replayed = nsteps - (nsteps + K - 1) // K
+        f = t_fwd / nsteps
+        reverse_step = (t_adj - f * (nsteps + replayed)) / nsteps
+        res[name] = {"forward_ms_per_step": f, "adjoint_ms_per_step": t_adj / nsteps,
                      "adjoint_vs_forward": t_adj / t_fwd, "reverse_vs_forward": (t_adj - t_fwd) / t_fwd,
+                     "reverse_step_vs_forward_step": reverse_step / f, "replayed_steps": replayed,
                      "launches_per_step": launches / nsteps, "ckpt_every": K, "steps": nsteps,
                      "device_bytes": dev_bytes, "J": J, "dJ_dsigma": g["sigma"]}
     return res
