@@ -698,17 +698,27 @@ __global__ void __launch_bounds__(kAT) k_rev_expand(const StepParams P, const fl
 // ahead so that their latency overlaps the current row: every plane row is
 // read from HBM once and only lambda is written.  The arithmetic is that of
 // the plane passes, term by term in the same order.
-constexpr int kTailRows = 100;  // ring rows of shared memory, kWin floats each
+// Ring sizes: a ring written by the stage at row s - a and last read, at
+// its lowest, at row s - b needs b - a + 1 rows when the writing stage runs
+// before the reading one in an iteration, b - a when after -- the fewest that
+// never overwrite a row still to be read, so that five CTAs fit per SM.
+constexpr int kTailRows = 75;  // ring rows of shared memory, kWin floats each
 enum TailRing : int {
-    kTDivub = 0, kTKb = 4, kTJxb = 8, kTJyb = 12, kTGxb = 16, kTGyb = 20, kTDpxb = 24, kTDpyb = 28,
-    kTRr = 32, kTRb = 36, kTGx = 40, kTGy = 44,  // 4-row rings
-    kTRrb = 48, kTRbb = 56,                      // 8-row rings
-    kTFb = 64                                    // 9 links x 4 rows
+    kTDivub = 0,                                                // L at s, R2 reads s - 2 .. s: 3 rows
+    kTKb = 3, kTJxb = 6, kTJyb = 9, kTRr = 12, kTRb = 15,       // R2 at s - 1, read down to s - 3: 3 rows
+    kTGxb = 18, kTGyb = 22, kTDpxb = 26, kTDpyb = 30,           // R2 at s - 1, R4 reads down to s - 4: 4 rows
+    kTGx = 34, kTGy = 36,                                       // R2 at s - 1, R3 reads s - 2: 2 rows
+    kTRrb = 38, kTRbb = 43,                                     // R2 at s - 1, R5 reads down to s - 5: 5 rows
+    kTFb = 48                                                   // 9 links; R4 at s - 3, R5 reads down to s - 5: 3 rows
 };
+static_assert(kTFb + 9 * 3 == kTailRows, "tail ring layout");
 constexpr int kTailSmem = kTailRows * kWin * 4;
+// slot of row r (r >= -64) in an M-row ring
+template <int M>
+__device__ __forceinline__ int tail_slot(int r) { return static_cast<int>(static_cast<unsigned>(r + 64 * M) % M); }
 
 template <bool W, bool EXPAND>
-__global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const float* __restrict__ S,
+__global__ void __launch_bounds__(kWin, 5) k_rev_tail(const StepParams P, const float* __restrict__ S,
                                                    float* __restrict__ lam, const int rows,
                                                    double* __restrict__ partials) {
     extern __shared__ __align__(16) float tsm[];
@@ -721,9 +731,11 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
     const bool own_col = t >= kHalo && t < kWin - kHalo && x0 + t - kHalo < nx;
     auto row_ok = [&](int r) { return !W || (r >= 0 && r < ny); };
     auto node = [&](int r) { return static_cast<size_t>(wrap_to(r, ny)) * nx + gx; };
-    auto ring4 = [&](int base, int r) { return tsm + (base + (r & 3)) * kWin; };
-    auto ring8 = [&](int base, int r) { return tsm + (base + (r & 7)) * kWin; };
-    auto fbr = [&](int i, int r) { return tsm + (kTFb + 4 * i + (r & 3)) * kWin; };
+    auto ring2 = [&](int base, int r) { return tsm + (base + tail_slot<2>(r)) * kWin; };
+    auto ring3 = [&](int base, int r) { return tsm + (base + tail_slot<3>(r)) * kWin; };
+    auto ring4 = [&](int base, int r) { return tsm + (base + tail_slot<4>(r)) * kWin; };
+    auto ring5 = [&](int base, int r) { return tsm + (base + tail_slot<5>(r)) * kWin; };
+    auto fbr = [&](int i, int r) { return tsm + (kTFb + 3 * i + tail_slot<3>(r)) * kWin; };
     // transpose of one component of the compact gradient, on ring rows
     // (the tap order and wall terms of Nbh::gradT)
     auto gradT = [&](auto rowp, bool xc, int y, float parity) {
@@ -780,13 +792,13 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
         for (int j = 0; j < 10; ++j) in4[j] = in4_next[j];
         if (k + 1 < iters) fetch(s + 1);
         // ---- L: div-u-bar of row s (the window: R2 reads it at t +- 1)
-        if (in_L(s)) ring4(kTDivub, s)[t] = dv;
+        if (in_L(s)) ring3(kTDivub, s)[t] = dv;
         __syncthreads();
         // ---- R2: reverse of the force at row s - 1 (k_rev_force)
         {
             const int y = s - 1;
             if (in_R2(y)) {
-                const auto dvr = [&](int r) { return ring4(kTDivub, r); };
+                const auto dvr = [&](int r) { return ring3(kTDivub, r); };
                 const float uxt = in2[0] + gradT(dvr, true, y, -1.0f);
                 const float uyt = in2[1] + gradT(dvr, false, y, -1.0f);
                 const float rr = in2[2], rb = in2[3];
@@ -798,9 +810,9 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
                 const float gxv = in2[8], gyv = in2[9], K = in2[10];
                 const float rhob = -(ux * uxt + uy * uyt) * ir + Gxt * P.gacc_x + Gyt * P.gacc_y;
                 const float gG = fmaf(Gxt, gxv, Gyt * gyv);
-                ring4(kTJxb, y)[t] = uxt * ir;
-                ring4(kTJyb, y)[t] = uyt * ir;
-                ring4(kTKb, y)[t] = P.half_sigma * gG;
+                ring3(kTJxb, y)[t] = uxt * ir;
+                ring3(kTJyb, y)[t] = uyt * ir;
+                ring3(kTKb, y)[t] = P.half_sigma * gG;
                 float gxb = in2[11], gyb = in2[12], rrb = in2[13], rbb = in2[14];
                 gxb += P.half_sigma * K * Gxt;
                 gyb += P.half_sigma * K * Gyt;
@@ -808,14 +820,14 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
                 rbb += rhob;
                 ring4(kTGxb, y)[t] = gxb;
                 ring4(kTGyb, y)[t] = gyb;
-                ring8(kTRrb, y)[t] = rrb;
-                ring8(kTRbb, y)[t] = rbb;
+                ring5(kTRrb, y)[t] = rrb;
+                ring5(kTRbb, y)[t] = rbb;
                 ring4(kTDpxb, y)[t] = in2[15];
                 ring4(kTDpyb, y)[t] = in2[16];
-                ring4(kTRr, y)[t] = rr;
-                ring4(kTRb, y)[t] = rb;
-                ring4(kTGx, y)[t] = gxv;
-                ring4(kTGy, y)[t] = gyv;
+                ring3(kTRr, y)[t] = rr;
+                ring3(kTRb, y)[t] = rb;
+                ring2(kTGx, y)[t] = gxv;
+                ring2(kTGy, y)[t] = gyv;
                 if (own_col && y >= y0 && y < y_end) {
                     acc_sigma += static_cast<double>(0.5f * K * gG);
                     acc_gx += static_cast<double>(rho * Gxt);
@@ -828,11 +840,11 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
         if (P.curvature_mode == 0) {
             const int y = s - 2;
             if (y >= y0 - 2 && y <= y_end + 1 && row_ok(y) && t >= 2 && t < kWin - 2) {
-                const auto kb = [&](int r) { return ring4(kTKb, r); };
+                const auto kb = [&](int r) { return ring3(kTKb, r); };
                 const float nxb = gradT(kb, true, y, 1.0f);
                 const float nyb = gradT(kb, false, y, -1.0f);
                 float tx, ty;
-                normalise_T(ring4(kTGx, y)[t], ring4(kTGy, y)[t], nxb, nyb, tx, ty);
+                normalise_T(ring2(kTGx, y)[t], ring2(kTGy, y)[t], nxb, nyb, tx, ty);
                 ring4(kTGxb, y)[t] -= tx;
                 ring4(kTGyb, y)[t] -= ty;
             }
@@ -847,12 +859,12 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
                        gradT([&](int r) { return ring4(kTGyb, r); }, false, y, 1.0f);
                 const float phb = gradT([&](int r) { return ring4(kTDpxb, r); }, true, y, 1.0f) +
                                   gradT([&](int r) { return ring4(kTDpyb, r); }, false, y, 1.0f);
-                const float rr = ring4(kTRr, y)[t], rb = ring4(kTRb, y)[t];
+                const float rr = ring3(kTRr, y)[t], rb = ring3(kTRb, y)[t];
                 const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
                 const float iden = 1.0f / ((a + b) * (a + b));
-                ring8(kTRrb, y)[t] += fmaf(rnb * 2.0f * b * iden, P.inv_rho0_r, phb * P.phip_r);
-                ring8(kTRbb, y)[t] += fmaf(rnb * -2.0f * a * iden, P.inv_rho0_b, phb * P.phip_b);
-                const float jxb = ring4(kTJxb, y)[t], jyb = ring4(kTJyb, y)[t];
+                ring5(kTRrb, y)[t] += fmaf(rnb * 2.0f * b * iden, P.inv_rho0_r, phb * P.phip_r);
+                ring5(kTRbb, y)[t] += fmaf(rnb * -2.0f * a * iden, P.inv_rho0_b, phb * P.phip_b);
+                const float jxb = ring3(kTJxb, y)[t], jyb = ring3(kTJyb, y)[t];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     float v = in4[1 + i];
@@ -873,8 +885,8 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
                     float common, cr, cb;
                     if (EXPAND) {
                         common = fbr(i, y)[t];
-                        cr = ring8(kTRrb, y)[t];
-                        cb = ring8(kTRbb, y)[t];
+                        cr = ring5(kTRrb, y)[t];
+                        cb = ring5(kTRbb, y)[t];
                     } else {
                         int li = i, sy = y + lcy(i), st = t + lcx(i);
                         if (W && (sy < 0 || sy >= ny)) {  // the node's own reversed link (half-way bounce-back)
@@ -883,8 +895,8 @@ __global__ void __launch_bounds__(kWin) k_rev_tail(const StepParams P, const flo
                             st = t;
                         }
                         common = fbr(li, sy)[st];
-                        cr = ring8(kTRrb, sy)[st];
-                        cb = ring8(kTRbb, sy)[st];
+                        cr = ring5(kTRrb, sy)[st];
+                        cb = ring5(kTRbb, sy)[st];
                     }
                     lam[static_cast<size_t>(i) * n + o] = common + cr;
                     lam[static_cast<size_t>(9 + i) * n + o] = common + cb;
@@ -960,11 +972,12 @@ cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double*
 // term.  (Fusing the reverse collision as a fourth stage was tried: its
 // registers left 12 warps per SM, and the four-stage kernel took 1.4x the
 // time of the passes it replaced.)
-constexpr int kHeadRows = 64;  // ring rows of shared memory, kWin floats each
+// Only the stencil stages' inputs live in rings (4 rows each: three rows a
+// stencil reads, one more for the mirrored row a wall adds ahead of the
+// schedule); Phi', G and u go to the planes alone.
+constexpr int kHeadRows = 40;  // ring rows of shared memory, kWin floats each
 enum HeadRing : int {
-    kHChr = 0, kHChb = 4, kHRr = 8, kHRb = 12, kHJx = 16, kHJy = 20, kHGx = 24, kHGy = 28, kHNx = 32, kHNy = 36,
-    kHGfx = 40, kHGfy = 44, kHUx = 48, kHUy = 52,  // 4-row rings
-    kHPhip = 56                                    // 8-row ring
+    kHChr = 0, kHChb = 4, kHRr = 8, kHRb = 12, kHJx = 16, kHJy = 20, kHGx = 24, kHGy = 28, kHNx = 32, kHNy = 36
 };
 
 template <bool W>
@@ -980,7 +993,6 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
     const bool own_col = t >= kHalo && t < kWin - kHalo && x0 + t - kHalo < nx;
     auto row_ok = [&](int r) { return !W || (r >= 0 && r < ny); };
     auto r4 = [&](int base, int r) { return hsm + (base + (r & 3)) * kWin; };
-    auto r8 = [&](int base, int r) { return hsm + (base + (r & 7)) * kWin; };
     // pre-collision populations of node (column xc, row y): f_i(r) = P_i(r - c_i),
     // half-way bounce-back beyond a wall (Nbh::gather)
     auto gather = [&](int y, float (&fr)[9], float (&fb)[9]) {
@@ -1039,7 +1051,6 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
                 const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
                 r4(kHChr, y)[t] = chr;
                 r4(kHChb, y)[t] = chb;
-                r8(kHPhip, y)[t] = phip;
                 r4(kHRr, y)[t] = rr;
                 r4(kHRb, y)[t] = rb;
                 r4(kHJx, y)[t] = ((f[1] + f[7]) + f[8]) - ((f[3] + f[5]) + f[4]);
@@ -1048,7 +1059,6 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
                     const int g = y == 0 ? -1 : ny;
                     r4(kHChr, g)[t] = chr;
                     r4(kHChb, g)[t] = chb;
-                    r8(kHPhip, g)[t] = phip;
                 }
                 if (owned(y)) {
                     const size_t o = static_cast<size_t>(y) * nx + xc;
@@ -1108,15 +1118,6 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
                 const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
                 const float ux = fmaf(0.5f, Gx, r4(kHJx, y)[t]) / rho;
                 const float uy = fmaf(0.5f, Gy, r4(kHJy, y)[t]) / rho;
-                r4(kHGfx, y)[t] = Gx;
-                r4(kHGfy, y)[t] = Gy;
-                r4(kHUx, y)[t] = ux;
-                r4(kHUy, y)[t] = uy;
-                if (W && (y == 0 || y == ny - 1)) {  // no-slip: u odd beyond the walls
-                    const int g = y == 0 ? -1 : ny;
-                    r4(kHUx, g)[t] = -ux;
-                    r4(kHUy, g)[t] = -uy;
-                }
                 if (owned(y)) {
                     const size_t o = static_cast<size_t>(y) * nx + xc;
                     S[kGX * n + o] = gx;
