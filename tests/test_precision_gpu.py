@@ -116,8 +116,8 @@ def test_fp16_close_to_fp32_on_full_size_field():
 def test_accuracy_table_buoyant_replica():
     """Per-field error of every storage form against the FP64 oracle on a
     128 x 128 replica of the buoyant-drops field after 2000 steps (the oracle
-    cannot run the 512^2 x 10k replica within a test).  Written to
-    gpurun_out/precision_accuracy.json when that directory exists."""
+    cannot run the 512^2 x 10k replica within a test).  Written as JSON to
+    the file named by the environment variable CMRT_ACCURACY_JSON, if set."""
     import json
     import os
     d, rn, u = I.buoyant_replica(side=128)
@@ -133,8 +133,8 @@ def test_accuracy_table_buoyant_replica():
     assert max(table["fp32"].values()) <= 1e-3
     assert max(table["fp16"].values()) <= BAR_LONG[FP16]
     assert max(table["bf16"].values()) <= BAR_LONG[BF16]
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "precision_accuracy.json"), "w") as fh:
+    out = os.environ.get("CMRT_ACCURACY_JSON")
+    if out:
+        with open(out, "w") as fh:
             json.dump({"workload": "buoyant replica 128x128, 1 drop, walls, g = 1e-6, 2000 steps",
                        "errors": table}, fh, indent=1)
