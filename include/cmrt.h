@@ -54,8 +54,9 @@ extern "C" {
 
 /* Raised whenever cmrt_params changes layout or a call is added or changes
  * meaning; bindings check it (cmrt_abi_version) before use.  6: per-context
- * step graphs (cmrt_set_graph_steps, cmrt_get_graph_steps). */
-#define CMRT_ABI_VERSION 6
+ * step graphs (cmrt_set_graph_steps, cmrt_get_graph_steps).  7: checkpoint
+ * and restart (cmrt_save_bytes, cmrt_save, cmrt_load). */
+#define CMRT_ABI_VERSION 7
 
 typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
 typedef struct cmrt_batch cmrt_batch; /* opaque, owned by the library */
@@ -182,6 +183,20 @@ cmrt_status cmrt_get_populations(cmrt_ctx* c, float* dst);
 /* Replaces the state by the pre-collision populations in src,
  * float[2][9][ny][nx], taken as the state at the current time. */
 cmrt_status cmrt_set_populations(cmrt_ctx* c, const float* src);
+
+/* Checkpoint and restart.  cmrt_save writes the context's state exactly as
+ * stored (FP32 populations, or the 16-bit records with their FP32 densities)
+ * with the time step and the lattice's size and storage form, so that
+ * cmrt_load on a context of the same size and storage form resumes the run
+ * bit for bit -- unlike a population export and import, which for 16-bit
+ * storage re-encodes.  The layout of the bytes is private to this library
+ * version (ABI version, sizes and a format tag are checked on load).
+ * dst/src: host or device memory of at least cmrt_save_bytes(c) bytes;
+ * CMRT_EINVAL if smaller, or on load if the record does not match the
+ * context.  Synchronises the stream. */
+size_t cmrt_save_bytes(const cmrt_ctx* c);
+cmrt_status cmrt_save(cmrt_ctx* c, void* dst, size_t bytes);
+cmrt_status cmrt_load(cmrt_ctx* c, const void* src, size_t bytes);
 
 /* Waits for all work queued on the context's stream. */
 cmrt_status cmrt_synchronize(cmrt_ctx* c);

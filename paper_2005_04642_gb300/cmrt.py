@@ -52,6 +52,9 @@ _SIGNATURES = [
     ("cmrt_diagnostics", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("cmrt_get_populations", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("cmrt_set_populations", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("cmrt_save_bytes", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("cmrt_save", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("cmrt_load", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("cmrt_synchronize", ctypes.c_int, [ctypes.c_void_p]),
     ("cmrt_time", ctypes.c_int64, [ctypes.c_void_p]),
     ("cmrt_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
@@ -89,7 +92,7 @@ _SIGNATURES = [
 CMRT_TUNE_FORCE = 1
 
 _lib = None
-ABI_VERSION = 6  # the layout of cmrt_params and the calls this binding was written for
+ABI_VERSION = 7  # the layout of cmrt_params and the calls this binding was written for
 
 
 def load(path: str = LIB_PATH):
@@ -446,6 +449,22 @@ class Lattice:
 
     def synchronize(self):
         cmrt_synchronize(self.ctx)
+
+    def save(self):
+        """Checkpoint of the state as stored, with its time (NumPy uint8 array)."""
+        lib = load()
+        buf = np.empty(lib.cmrt_save_bytes(self.ctx), dtype=np.uint8)
+        _check(lib.cmrt_save(self.ctx, buf.ctypes.data, buf.nbytes), self.ctx)
+        return buf
+
+    def load(self, buf):
+        """Restart from a checkpoint of save() (a NumPy array or a CUDA tensor)."""
+        if hasattr(buf, "data_ptr"):
+            ptr, n = buf.data_ptr(), buf.numel() * buf.element_size()
+        else:
+            buf = np.ascontiguousarray(buf, dtype=np.uint8)
+            ptr, n = buf.ctypes.data, buf.nbytes
+        _check(load().cmrt_load(self.ctx, ptr, n), self.ctx)
 
     def step_vjp(self, lam_next):
         """dJ/df(t) from dJ/df(t+1) for one step at the current state; returns

@@ -776,6 +776,67 @@ cmrt_status cmrt_set_populations(cmrt_ctx* h, const float* src) {
     return CMRT_OK;
 }
 
+// Checkpoint record: this header, then the state buffer's bytes as stored.
+struct SaveHeader {
+    uint64_t tag;
+    int32_t abi, nx, ny, precision, wall_y, stencil_order;
+    int64_t t;
+    uint64_t state_bytes;
+};
+constexpr uint64_t kSaveTag = 0x3156415354524d43ull;  // "CMRTSAV1"
+
+size_t cmrt_save_bytes(const cmrt_ctx* h) {
+    if (!h) return 0;
+    return sizeof(SaveHeader) + cells(h->c) * cmrt::state_node_bytes(h->c.p.precision);
+}
+
+cmrt_status cmrt_save(cmrt_ctx* h, void* dst, size_t bytes) {
+    Ctx* c = live(h);
+    if (!c) return CMRT_ESTATE;
+    if (!dst) return fail(c, CMRT_EINVAL, "dst is NULL");
+    const size_t state = cells(*c) * cmrt::state_node_bytes(c->p.precision);
+    if (bytes < sizeof(SaveHeader) + state)
+        return fail(c, CMRT_EINVAL, "a checkpoint needs %zu bytes, got %zu", sizeof(SaveHeader) + state, bytes);
+    if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
+    const SaveHeader hd{kSaveTag, CMRT_ABI_VERSION, c->p.nx, c->p.ny, c->p.precision, c->p.wall_y,
+                        c->p.stencil_order, c->t, static_cast<uint64_t>(state)};
+    char* out = static_cast<char*>(dst);
+    if (is_device_ptr(dst)) CK(c, cudaMemcpyAsync(out, &hd, sizeof hd, cudaMemcpyHostToDevice, c->stream));
+    else std::memcpy(out, &hd, sizeof hd);
+    CK(c, cudaMemcpyAsync(out + sizeof hd, c->buf[c->cur], state, cudaMemcpyDefault, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return CMRT_OK;
+}
+
+cmrt_status cmrt_load(cmrt_ctx* h, const void* src, size_t bytes) {
+    Ctx* c = live(h);
+    if (!c) return CMRT_ESTATE;
+    if (!src) return fail(c, CMRT_EINVAL, "src is NULL");
+    if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch follows the batch's time", c->member);
+    if (bytes < sizeof(SaveHeader)) return fail(c, CMRT_EINVAL, "%zu bytes hold no checkpoint", bytes);
+    if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
+    SaveHeader hd{};
+    const char* in = static_cast<const char*>(src);
+    if (is_device_ptr(src)) {
+        CK(c, cudaMemcpyAsync(&hd, in, sizeof hd, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(&hd, in, sizeof hd);
+    }
+    const size_t state = cells(*c) * cmrt::state_node_bytes(c->p.precision);
+    if (hd.tag != kSaveTag || hd.abi != CMRT_ABI_VERSION)
+        return fail(c, CMRT_EINVAL, "not a checkpoint of this library version");
+    if (hd.nx != c->p.nx || hd.ny != c->p.ny || hd.precision != c->p.precision || hd.wall_y != c->p.wall_y ||
+        hd.stencil_order != c->p.stencil_order || hd.state_bytes != state)
+        return fail(c, CMRT_EINVAL, "the checkpoint is of a %d x %d lattice (storage %d, walls %d, order %d)", hd.nx,
+                    hd.ny, hd.precision, hd.wall_y, hd.stencil_order);
+    if (bytes < sizeof hd + state) return fail(c, CMRT_EINVAL, "the checkpoint is cut short (%zu bytes)", bytes);
+    CK(c, cudaMemcpyAsync(c->buf[c->cur], in + sizeof hd, state, cudaMemcpyDefault, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->t = hd.t;
+    return CMRT_OK;
+}
+
 cmrt_status cmrt_synchronize(cmrt_ctx* h) {
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;

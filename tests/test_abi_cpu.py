@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(cm):
 
 
 def test_abi_version_and_struct_size(cm):
-    assert cm.cmrt_abi_version() == 6
+    assert cm.cmrt_abi_version() == 7
     assert cm.load().cmrt_params_size() == ctypes.sizeof(cm.cmrt_params)
 
 
@@ -79,6 +79,9 @@ def test_null_context_calls(cm):
     assert lib.cmrt_step(None, 1) == cm.CMRT_ESTATE
     assert lib.cmrt_set_graph_steps(None, 2) == cm.CMRT_ESTATE
     assert lib.cmrt_get_graph_steps(None) == -1
+    assert lib.cmrt_save_bytes(None) == 0
+    assert lib.cmrt_save(None, None, 0) == cm.CMRT_ESTATE
+    assert lib.cmrt_load(None, None, 0) == cm.CMRT_ESTATE
     assert lib.cmrt_time(None) == -1
     assert lib.cmrt_launch_count(None) == -1
     lib.cmrt_destroy(None)  # no-op
