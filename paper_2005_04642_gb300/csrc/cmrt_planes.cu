@@ -37,6 +37,7 @@
 // per CTA (FP32 within a warp, FP64 from there) and accumulated across steps
 // in a per-CTA FP64 slot (no atomics: every launch of a pass uses the same
 // grid, and the slots are summed once at the end).
+#include <atomic>
 #include <type_traits>
 
 #include "cmrt_device.cuh"
@@ -942,15 +943,15 @@ bool use_fused(const StepParams& P) {
 
 template <bool W, bool EXPAND>
 cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double* partials, cudaStream_t s) {
-    static unsigned long long configured = 0;  // the shared-memory opt-in, once per device
+    static std::atomic<unsigned long long> configured{0};  // the shared-memory opt-in, once per device (any thread)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
-    if (!(configured & bit)) {
+    if (!(configured.load() & bit)) {
         e = cudaFuncSetAttribute(k_rev_tail<W, EXPAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem);
         if (e != cudaSuccess) return e;
-        configured |= bit;
+        configured.fetch_or(bit);
     }
     const int rows = tail_rows(P.nx, P.ny);
     const dim3 g(static_cast<unsigned>((P.nx + kTileX - 1) / kTileX), static_cast<unsigned>((P.ny + rows - 1) / rows));

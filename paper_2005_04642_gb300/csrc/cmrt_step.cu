@@ -34,6 +34,8 @@
 // small, so FP32 rounding stays at the level of population storage.  The
 // reconstruction M^{-1} dm is grouped by the parity of each column k^(p)
 // under c -> -c, which the k vectors of App. A have by construction.
+#include <atomic>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -808,13 +810,13 @@ __global__ void __launch_bounds__(kStepThreads, pass_ctas_per_sm<L>(Pass::Step))
 
 template <class L, bool VEC>
 cudaError_t batch_configure(int dev, int* ctas_per_sm) {
-    static unsigned long long configured = 0;
+    static std::atomic<unsigned long long> configured{0};  // per device, set from any host thread
     const unsigned long long bit = 1ull << (dev & 63);
     cudaError_t e = cudaSuccess;
-    if (!(configured & bit)) {
+    if (!(configured.load() & bit)) {
         e = cudaFuncSetAttribute(k_batch<L, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geometry<L>::kBytes);
         if (e != cudaSuccess) return e;
-        configured |= bit;
+        configured.fetch_or(bit);
     }
     if (ctas_per_sm)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_batch<L, VEC>, kStepThreads,
@@ -867,16 +869,16 @@ template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 cudaError_t launch_one(const void* src, void* dst, const StepParams& P, int rows, FieldOut fo, unsigned* flag,
                        double* partials, cudaStream_t s) {
     // the shared-memory opt-in is per kernel and per device: set it once for each
-    static unsigned long long configured = 0;
+    static std::atomic<unsigned long long> configured{0};  // per device, set from any host thread
     const int smem = Geometry<L>::kBytes;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
-    if (!(configured & bit)) {
+    if (!(configured.load() & bit)) {
         e = cudaFuncSetAttribute(k_chain<L, VEC, WALLS, MODE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured |= bit;
+        configured.fetch_or(bit);
     }
     return launch_pdl(k_chain<L, VEC, WALLS, MODE, PRE>, chain_grid(P.nx, P.ny, rows), dim3(pass_threads(MODE)), smem,
                       s, static_cast<const char*>(src), static_cast<char*>(dst), P, rows, fo, flag, partials);
