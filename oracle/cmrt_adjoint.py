@@ -105,15 +105,16 @@ def stream_T(adj, p: O.Params):
 
 
 def _normalise_T(gx, gy, bx, by):
-    """Adjoint of g -> g / max(|g|, eps) (the recolour direction e, and minus
-    the unit normal): (I - e e^T) b / |g| above eps, b / eps below."""
+    """Adjoint of g -> g / |g| with the guard of the unit normal (the recolour
+    direction e, and minus the unit normal): (I - e e^T) b / |g| where
+    |g| >= NORMAL_TAU, and 0 below it, where the map is the constant 0."""
     mag = np.sqrt(gx * gx + gy * gy)
-    big = mag > O.NORMAL_EPS
+    big = mag >= O.NORMAL_TAU
     safe = np.where(big, mag, 1.0)
     ex, ey = gx / safe, gy / safe
     dot = ex * bx + ey * by
-    outx = np.where(big, (bx - ex * dot) / safe, bx / O.NORMAL_EPS)
-    outy = np.where(big, (by - ey * dot) / safe, by / O.NORMAL_EPS)
+    outx = np.where(big, (bx - ex * dot) / safe, 0.0)
+    outy = np.where(big, (by - ey * dot) / safe, 0.0)
     return outx, outy
 
 
@@ -137,9 +138,7 @@ def step_vjp(R, B, lamR, lamB, p: O.Params):
     S = O.modal_sources(Gx, Gy, cxx, cyy, cxy, p)
     mplus = O.relax(m, meq, S, lam3, p)
     fplus = O.reconstruct(mplus, p)
-    mag = np.sqrt(d.gnx ** 2 + d.gny ** 2)
-    inv = 1.0 / np.maximum(mag, O.NORMAL_EPS)
-    ex, ey = d.gnx * inv, d.gny * inv
+    ex, ey = -d.nhx, -d.nhy
 
     grads = {k: 0.0 for k in PARAM_NAMES}
     z = np.zeros_like(rho)
@@ -256,7 +255,7 @@ def step_vjp(R, B, lamR, lamB, p: O.Params):
     grads["g_acc_x"] += float(np.sum(rho * Gx_bar))
     grads["g_acc_y"] += float(np.sum(rho * Gy_bar))
 
-    # -- curvature K = div n-hat, unit normal n-hat = -g / max(|g|, eps)
+    # -- curvature K = div n-hat, unit normal n-hat = -g / |g| (0 below the guard)
     if p.curvature_mode == 0:
         nx_bar = gradient_T(K_bar, None, p, parity=1)
         ny_bar = gradient_T(None, K_bar, p, parity=-1)

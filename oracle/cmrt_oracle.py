@@ -147,13 +147,15 @@ class Params:
         return self.rho0_r / self.rho0_b
 
 
-# Regularisation of the unit normal: n-hat = -grad rho^N / max(|grad rho^N|, eps).
-# The paper's n-hat = -grad rho^N / |grad rho^N| (Sec. 2) is undefined where the
-# gradient vanishes, e.g. at the centre of a symmetric drop, where rho_R rho_B /
-# rho need not be small: there the recolour direction would be set by round-off.
-# Reading: below eps the normal shrinks smoothly to zero (no segregation where
-# there is no interface); above eps it is the paper's unit vector.
-NORMAL_EPS = 1e-4
+# Guard of the unit normal.  The paper's n-hat = -grad rho^N / |grad rho^N|
+# (Sec. 2) has no direction where the colour gradient vanishes: at the centre
+# of a symmetric drop and at the symmetry points between drops.  Reading: below
+# NORMAL_TAU the normal is zero (no recolour bias, no contribution to K);
+# at and above it, it is the paper's unit vector.  The threshold is far below
+# the colour gradient of any resolved interface (an interface of width W has
+# |grad rho^N| ~ 2/W at its centre) and above the round-off of the gradient
+# at a drop's centre, where the same noise would otherwise set the direction.
+NORMAL_TAU = 1e-9
 
 
 # ---------------------------------------------------------------------------
@@ -273,11 +275,12 @@ def gradient(field_, p: Params, parity=1, order=2):
 
 
 def unit_normal(gx, gy, p: Params):
-    """n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised as
-    -grad rho^N / max(|grad rho^N|, 1e-4) where the gradient vanishes."""
+    """n-hat = -grad rho^N / |grad rho^N| (Sec. 2) where |grad rho^N| >= NORMAL_TAU,
+    and 0 where the gradient is below that guard (no direction)."""
     dt = p.dtype
     mag = np.sqrt(gx * gx + gy * gy)
-    inv = dt(1.0) / np.maximum(mag, dt(NORMAL_EPS))
+    big = mag >= dt(NORMAL_TAU)
+    inv = np.where(big, dt(1.0) / np.where(big, mag, dt(1.0)), dt(0.0))
     return -gx * inv, -gy * inv
 
 

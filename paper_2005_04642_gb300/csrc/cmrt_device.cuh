@@ -74,11 +74,14 @@ __device__ __forceinline__ float ddy(float n, float s, float ne, float nw, float
     return (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * ((ne - se) + (nw - sw));
 }
 
-// Regularisation of the unit normal, n-hat = -grad rho^N / max(|grad rho^N|, eps):
-// the paper's unit vector wherever an interface is resolved, shrinking smoothly
-// to zero where the colour gradient vanishes (there its direction would be
-// set by round-off).
-constexpr float kNormalEps = 1e-4f;
+// Guard of the unit normal n-hat = -grad rho^N / |grad rho^N| (Sec. 2), which
+// has no direction where the colour gradient vanishes (at the centre of a
+// symmetric drop, at the symmetry points between drops): below kNormalTau
+// the normal is taken as zero, so such a node gets no recolour bias and adds
+// nothing to K.  The threshold sits above the FP32 round-off of the gradient
+// (taken on the minority colour fraction, whose spacing is relative) and far
+// below the gradient of any resolved interface.
+constexpr float kNormalTau = 1e-9f;
 
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 

@@ -208,18 +208,19 @@ __device__ __forceinline__ float sum9f(const float (&v)[9]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
 }
 
-// adjoint of g -> g / max(|g|, eps): (I - e e^T) b / |g| above eps, b / eps below
+// adjoint of g -> g / |g| (0 below kNormalTau): (I - e e^T) b / |g| above the
+// threshold, 0 below it (the map is constant there)
 __device__ __forceinline__ void normalise_T(float gx, float gy, float bx, float by, float& ox, float& oy) {
     const float mag2 = fmaf(gx, gx, gy * gy);
-    if (mag2 >= kNormalEps * kNormalEps) {
+    if (mag2 >= kNormalTau * kNormalTau) {
         const float inv = rsqrtf(mag2);
         const float ex = gx * inv, ey = gy * inv;
         const float dot = fmaf(ex, bx, ey * by);
         ox = (bx - ex * dot) * inv;
         oy = (by - ey * dot) * inv;
     } else {
-        ox = bx * (1.0f / kNormalEps);
-        oy = by * (1.0f / kNormalEps);
+        ox = 0.0f;
+        oy = 0.0f;
     }
 }
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kAT) k_fwd_normal(const StepParams P, float* _
     // zero): the same stencil, evaluated on the fraction that is small here
     const size_t o = L.o;
     float gx, gy;
-    const bool red_minor = S[kCHR * L.n + o] < S[kCHB * L.n + o];
+    const bool red_minor = S[kCHR * L.n + o] <= 0.5f;
     const float* ch = S + (red_minor ? kCHR : kCHB) * L.n;
     L.template grad<ORDER>(ch, 1.0f, gx, gy);
     gx *= red_minor ? 2.0f : -2.0f;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kAT) k_fwd_normal(const StepParams P, float* _
 
 __device__ __forceinline__ void normal_of(float gx, float gy, float& nx, float& ny) {
     const float mag2 = fmaf(gx, gx, gy * gy);
-    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    const float inv = (mag2 >= kNormalTau * kNormalTau) ? rsqrtf(mag2) : 0.0f;
     nx = -gx * inv;
     ny = -gy * inv;
 }
@@ -393,7 +394,7 @@ __device__ __forceinline__ void rev_collide_node(const float (&f)[9], float rr, 
         fp[i] = s;
     }
     const float mag2 = fmaf(gx, gx, gy * gy);
-    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    const float inv = (mag2 >= kNormalTau * kNormalTau) ? rsqrtf(mag2) : 0.0f;
     const float ex = gx * inv, ey = gy * inv;
     const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * ir;  // phi_i = w_i phim (i != 0)
     const float seg = P.beta * rr * rb * ir;
@@ -1076,7 +1077,7 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
         {
             const int y = s - 2;
             if (y >= y0 - 2 && y <= y_end + 1 && row_ok(y) && t >= 2 && t < kWin - 2) {
-                const bool red_minor = r4(kHChr, y)[t] < r4(kHChb, y)[t];
+                const bool red_minor = r4(kHChr, y)[t] <= 0.5f;
                 float gx, gy;
                 if (red_minor) grad([&](int r) { return r4(kHChr, r); }, y, gx, gy);
                 else grad([&](int r) { return r4(kHChb, r); }, y, gx, gy);
@@ -1245,10 +1246,10 @@ __global__ void __launch_bounds__(kAT) k_step_planes(const float* __restrict__ p
     float fp[9];
     collide_increment(f, rr, rb, rho, nu, S[kUX * L.n + o], S[kUY * L.n + o], S[kGFX * L.n + o],
                       S[kGFY * L.n + o], dPx, dPy, dux + duy, P, fp);
-    // recolour along e = grad rho^N / max(|grad rho^N|, eps) (Eq. eq_re_color)
+    // recolour along e = grad rho^N / |grad rho^N| (Eq. eq_re_color; 0 below kNormalTau)
     const float gx = S[kGX * L.n + o], gy = S[kGY * L.n + o];
     const float mag2 = fmaf(gx, gx, gy * gy);
-    const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+    const float inv = (mag2 >= kNormalTau * kNormalTau) ? rsqrtf(mag2) : 0.0f;
     const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
     const float sg = P.beta * (rr * rb) * inv_rho * phim * inv;
     store_recoloured_f32(dst + o, L.n, fp, rr, rb, inv_rho, sg * gx, sg * gy);

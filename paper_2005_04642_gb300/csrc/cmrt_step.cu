@@ -48,11 +48,14 @@ constexpr int kPlanes = 18;
 // Rings of stage results, each holding only the rows its readers need (a
 // row is one float per window column; fields x and y interleaved by row):
 //   grad rho^N  4 rows  (B writes row s - 2 while C may still read s - 4)
-//   n-hat       4 rows + the mirrored row ny beyond a wall
+//   n-hat       4 rows
 //   G           4 rows  (C writes row s - 3 while D may still read s - 5)
-//   u           4 rows + the mirrored row ny
-constexpr int kBFloats = (4 * 2 + 5 * 2) * kWin;  // grad rho^N, n-hat
-constexpr int kCFloats = (4 * 2 + 5 * 2) * kWin;  // G, u
+//   u           4 rows
+// The mirrored rows beyond a wall share these slots: row -1 takes the slot
+// of row 3, and row ny the slot of row ny - 4, written one row iteration
+// after row ny - 1, when no stage reads row ny - 4 any more.
+constexpr int kBFloats = (4 * 2 + 4 * 2) * kWin;  // grad rho^N, n-hat
+constexpr int kCFloats = (4 * 2 + 4 * 2) * kWin;  // G, u
 
 // The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
 // kThreads ("front") stream the rows in and run stages A-B, while the other
@@ -330,9 +333,9 @@ template <class L>
 struct Geometry {
     static constexpr int kPopBytes = kRing * L::kSlotBytes;
     // ring A: Phi' over 8 rows (ring Q; D's stencil reads it) and chi_R, rho,
-    // j_x, j_y over 4 rows (B and C read them; D recomputes rho^N)
+    // j_x, j_y, chi_B over 4 rows (B and C read them; D recomputes rho^N)
     static constexpr int kQFloats = 8 * kWin;
-    static constexpr int kAFloats = 4 * 4 * kWin;
+    static constexpr int kAFloats = 5 * 4 * kWin;
     static constexpr int kBytes = kPopBytes + 4 * (kQFloats + kAFloats + kBFloats + kCFloats);
 };
 
@@ -347,21 +350,20 @@ struct Rings {
     float* a;
     float* b;
     float* c;
-    int ghost;  // ny with walls W (n-hat and u keep the mirrored row ny in slot 4)
     // population ring slot k (rows map to slots in order of arrival)
     __device__ __forceinline__ const char* slot(int k) const { return pop + k * L::kSlotBytes; }
-    // ring A fields: the red fraction chi_R = a / (a + b) (a = rho_R / rho0_r,
-    // b = rho_B / rho0_b; rho^N = 2 chi_R - 1, Eq. equ_rhoN_def)
-    __device__ __forceinline__ float* chiR(int row) const { return a + ((row & 3) * 4 + 0) * kWin; }
+    // ring A fields: the colour fractions chi_R = a / (a + b) and chi_B = b / (a + b)
+    // (a = rho_R / rho0_r, b = rho_B / rho0_b; rho^N = chi_R - chi_B, Eq. equ_rhoN_def)
+    __device__ __forceinline__ float* chiR(int row) const { return a + ((row & 3) * 5 + 0) * kWin; }
+    __device__ __forceinline__ float* chiB(int row) const { return a + ((row & 3) * 5 + 4) * kWin; }
     __device__ __forceinline__ float* phip(int row) const { return q + (row & 7) * kWin; }
-    __device__ __forceinline__ float* rho(int row) const { return a + ((row & 3) * 4 + 1) * kWin; }
-    __device__ __forceinline__ float* jx(int row) const { return a + ((row & 3) * 4 + 2) * kWin; }
-    __device__ __forceinline__ float* jy(int row) const { return a + ((row & 3) * 4 + 3) * kWin; }
-    __device__ __forceinline__ int slot4(int row) const { return (W && row == ghost) ? 4 : (row & 3); }
+    __device__ __forceinline__ float* rho(int row) const { return a + ((row & 3) * 5 + 1) * kWin; }
+    __device__ __forceinline__ float* jx(int row) const { return a + ((row & 3) * 5 + 2) * kWin; }
+    __device__ __forceinline__ float* jy(int row) const { return a + ((row & 3) * 5 + 3) * kWin; }
     __device__ __forceinline__ float* grad(int row, int f) const { return b + ((row & 3) * 2 + f) * kWin; }
-    __device__ __forceinline__ float* nh(int row, int f) const { return b + (8 + slot4(row) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* nh(int row, int f) const { return b + (8 + (row & 3) * 2 + f) * kWin; }
     __device__ __forceinline__ float* G(int row, int f) const { return c + ((row & 3) * 2 + f) * kWin; }
-    __device__ __forceinline__ float* u(int row, int f) const { return c + (8 + slot4(row) * 2 + f) * kWin; }
+    __device__ __forceinline__ float* u(int row, int f) const { return c + (8 + (row & 3) * 2 + f) * kWin; }
 };
 
 // The rings carved out of a CTA's dynamic shared memory.
@@ -374,7 +376,6 @@ __device__ __forceinline__ Rings<L, W> make_rings(char* smem, int ny) {
     R.a = R.q + G::kQFloats;
     R.b = R.a + G::kAFloats;
     R.c = R.b + kBFloats;
-    R.ghost = ny;
     return R;
 }
 
@@ -496,23 +497,27 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                              (((fr[5] + fb[5]) + (fr[7] + fb[7])) + (fr[6] + fb[6]));
             const float a = rr * P.inv_rho0_r;
             const float b = rb * P.inv_rho0_b;
-            // red fraction: rho^N = 2 chi_R - 1 (Eq. equ_rhoN_def); near pure
-            // blue chi_R is small and keeps the digits that rho^N, stored in
-            // FP32 next to -1, would lose
+            // colour fractions: rho^N = 2 chi_R - 1 = 1 - 2 chi_B (Eq. equ_rhoN_def);
+            // the smaller of the two keeps the digits that rho^N, stored in FP32
+            // next to -1 or +1, would lose
             const float inv_ab = rcp(a + b);
             const float chr = a * inv_ab;
+            const float chb = b * inv_ab;
             const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
             R.chiR(ya)[t] = chr;
+            R.chiB(ya)[t] = chb;
             R.phip(ya)[t] = phip;
             R.rho(ya)[t] = rr + rb;
             R.jx(ya)[t] = jx;
             R.jy(ya)[t] = jy;
             if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
                 R.chiR(-1)[t] = chr;
+                R.chiB(-1)[t] = chb;
                 R.phip(-1)[t] = phip;
             }
             if (WALLS && ya == ny - 1) {  // even mirror beyond y = ny - 1/2
                 R.chiR(ny)[t] = chr;
+                R.chiB(ny)[t] = chb;
                 R.phip(ny)[t] = phip;
             }
         }
@@ -521,13 +526,18 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
     auto stage_b = [&](const int s) {
         const int yb = s - 2;
         if (yb >= y0 - 2 && yb <= y_end + 1 && row_ok(yb) && t >= 2 && t < kWin - 2) {
-            // grad rho^N = 2 grad chi_R (the stencil weights sum to zero)
-            auto ch_row = [&](int r) { return R.chiR(r); };
-            const float gx = 2.0f * ddx_at(ch_row, yb, t);
-            const float gy = 2.0f * ddy_at(ch_row, yb, t);
-            // n-hat = -grad rho^N / |grad rho^N| (Sec. 2), regularised below kNormalEps
+            // grad rho^N = 2 grad chi_R = -2 grad chi_B (the stencil weights sum
+            // to zero), taken on the node's minority fraction, whose FP32 spacing
+            // is relative: the gradient stays accurate where it is small
+            const bool use_b = R.chiR(yb)[t] > 0.5f;
+            const int foff = use_b ? 4 * kWin : 0;
+            auto ch_row = [&](int r) { return R.chiR(r) + foff; };
+            const float two = use_b ? -2.0f : 2.0f;
+            const float gx = two * ddx_at(ch_row, yb, t);
+            const float gy = two * ddy_at(ch_row, yb, t);
+            // n-hat = -grad rho^N / |grad rho^N| (Sec. 2); no direction below kNormalTau
             const float mag2 = fmaf(gx, gx, gy * gy);
-            const float inv = (mag2 >= kNormalEps * kNormalEps) ? rsqrtf(mag2) : (1.0f / kNormalEps);
+            const float inv = (mag2 >= kNormalTau * kNormalTau) ? rsqrtf(mag2) : 0.0f;
             const float nhx = -gx * inv;
             const float nhy = -gy * inv;
             R.grad(yb, 0)[t] = gx;
@@ -538,10 +548,12 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                 R.nh(-1, 0)[t] = nhx;
                 R.nh(-1, 1)[t] = -nhy;
             }
-            if (WALLS && yb == ny - 1) {
-                R.nh(ny, 0)[t] = nhx;
-                R.nh(ny, 1)[t] = -nhy;
-            }
+        }
+        if (WALLS && yb == ny && t >= 2 && t < kWin - 2) {
+            // reflected normal beyond the top wall, from row ny - 1 (written by
+            // this thread one iteration ago) into the slot of row ny - 4
+            R.nh(ny, 0)[t] = R.nh(ny - 1, 0)[t];
+            R.nh(ny, 1)[t] = -R.nh(ny - 1, 1)[t];
         }
     };
     // ---------------- stage C: curvature, force, velocity at row yc = s - 3 (tile + 1)
@@ -574,10 +586,12 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                 R.u(-1, 0)[t] = -ux;
                 R.u(-1, 1)[t] = -uy;
             }
-            if (WALLS && yc == ny - 1) {
-                R.u(ny, 0)[t] = -ux;
-                R.u(ny, 1)[t] = -uy;
-            }
+        }
+        if (WALLS && yc == ny && t >= 3 && t < kWin - 3) {
+            // odd mirror of u beyond the top wall, from row ny - 1 (this thread,
+            // one iteration ago) into the slot of row ny - 4
+            R.u(ny, 0)[t] = -R.u(ny - 1, 0)[t];
+            R.u(ny, 1)[t] = -R.u(ny - 1, 1)[t];
         }
     };
     // ---------------- stage D: collide, recolour, store at row yd = s - 4 (tile); ks = slot of row s
