@@ -214,16 +214,24 @@ size_t cmrt_device_bytes(const cmrt_ctx* c);
  *
  * The paper has no counterpart: this is a library facility.  It is for
  * callers that cannot allocate device memory when they need the reduction:
- * code recording a CUDA graph, code under a hard device-memory cap or a
- * custom allocator, code that must not let cudaMalloc/cudaFree synchronise
- * the device.  It needs no context and calls no allocating routine.
+ * code under a hard device-memory cap or a custom allocator that forbids
+ * ad-hoc allocations, and code that must not let cudaMalloc/cudaFree
+ * synchronise the whole device in the middle of a pipeline.  It needs no
+ * context and calls no allocating routine.
  *
- * p:     parameters of the lattice (validated as for cmrt_init).
+ * p:     parameters of the lattice (validated as for cmrt_init);
+ *        stencil_order 6 is rejected (its passes need a context's planes).
  * pops:  pre-collision populations float[2][9][ny][nx] in DEVICE memory of
- *        the current device (e.g. from cmrt_get_populations); host memory is
- *        rejected with CMRT_EINVAL, since copying it would need a buffer.
+ *        the current device (e.g. from cmrt_get_populations), 16-byte aligned
+ *        when nx is a multiple of 4 and 4-byte aligned otherwise.  Host
+ *        memory (copying it would need a buffer), memory of another device
+ *        and a misaligned address are rejected with CMRT_EINVAL before any
+ *        launch.
  * out:   host double[6], the same quantities as cmrt_diagnostics.
- * cuda_stream: stream the reduction runs on; the call synchronises it.
+ * cuda_stream: stream the reduction runs on.  The call waits for this
+ *        stream before it returns (the result is copied to the host), so a
+ *        stream that is capturing a CUDA graph is rejected with CMRT_EINVAL
+ *        before anything is enqueued.
  *
  * Scratch: a fixed area compiled into the library (384 KiB of device memory
  * on every GPU that loads it, held until exit) with room for 8192 partial
@@ -231,8 +239,10 @@ size_t cmrt_device_bytes(const cmrt_ctx* c);
  * lattices are rejected with CMRT_EINVAL.  All calls share that area: calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  The first call on a device looks up the
- * area's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Returns CMRT_ENONFINITE when out[5] > 0. */
+ * area's device address (cudaGetSymbolAddress) and keeps it for the life of
+ * the process: make that first call before any stream capture, and do not
+ * use this entry point on a device after cudaDeviceReset.  Returns
+ * CMRT_ENONFINITE when out[5] > 0. */
 cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const float* pops, double out[6], void* cuda_stream);
 
 /* ------------------------------------------------------------------------

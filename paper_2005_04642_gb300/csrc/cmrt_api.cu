@@ -878,12 +878,14 @@ const char* cmrt_last_error(const cmrt_ctx* h) {
 // Diagnostics without any allocation.
 //
 // Some callers cannot allocate device memory at the point where they want a
-// reduction of the state: code recording a CUDA graph (cudaMalloc is not a
-// capturable operation), code running under a hard device-memory cap or a
-// custom allocator that forbids ad-hoc allocations, and code that must not
-// let cudaMalloc/cudaFree synchronise the device in the middle of a pipeline.
-// For them this entry point works on caller-owned populations and uses a
-// fixed scratch area compiled into the library instead of a context.
+// reduction of the state: code under a hard device-memory cap or a custom
+// allocator that forbids ad-hoc allocations, and code that must not let
+// cudaMalloc/cudaFree synchronise the whole device in the middle of a
+// pipeline.  For them this entry point works on caller-owned populations and
+// uses a fixed scratch area compiled into the library instead of a context.
+// It waits for its own stream (the result is copied to the host), so a
+// stream that is recording a CUDA graph is refused before anything is
+// enqueued.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -911,6 +913,33 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
         cudaGetLastError();
         return fail(nullptr, CMRT_ECUDA, "no usable current CUDA device");
     }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the call ends by waiting for its stream, which a capturing stream does
+    // not allow: refuse before anything is enqueued, leaving the capture intact
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, CMRT_EINVAL, "the stream's capture status cannot be queried");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(nullptr, CMRT_EINVAL, "the stream is capturing a CUDA graph; this call waits for its stream");
+    // the pass reads the planes with 16-byte copies when nx is a multiple of 4
+    // (4-byte copies otherwise): the base address must allow them
+    const uintptr_t align = (p->nx % 4 == 0) ? 16 : 4;
+    if (reinterpret_cast<uintptr_t>(pops) % align != 0)
+        return fail(nullptr, CMRT_EINVAL, "pops must be %u-byte aligned for nx = %d", static_cast<unsigned>(align),
+                    p->nx);
+    {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, pops) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(nullptr, CMRT_EINVAL, "pops must be device memory of the current device");
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != dev)
+            return fail(nullptr, CMRT_EINVAL, "pops is memory of device %d, the current device is %d", a.device, dev);
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+            return fail(nullptr, CMRT_EINVAL, "pops must be device memory of the current device");
+    }
     double* scratch = nullptr;
     {
         // set-up, once per device, with that device current: the host-side name
@@ -926,7 +955,6 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
         }
         scratch = g_noalloc_ptr[dev];
     }
-    if (!is_device_ptr(pops)) return fail(nullptr, CMRT_EINVAL, "pops must be device memory of the current device");
     int sms = 1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -945,7 +973,6 @@ extern "C" cmrt_status cmrt_diagnostics_noalloc(const cmrt_params* p, const floa
         return fail(nullptr, CMRT_EINVAL, "lattice %d x %d needs %d partial blocks; the scratch area holds %d", p->nx,
                     p->ny, nblocks, kNoAllocMaxBlocks);
     const StepParams sp = derive(*p);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     double* result = scratch + static_cast<size_t>(kNoAllocMaxBlocks) * cmrt::kDiagSlots;
     // every partial slot used below is written by its CTA and the result by the
     // reduction, so nothing left from an earlier call is read

@@ -103,3 +103,4 @@ def test_pinned_host_buffers_are_read_and_written_in_place(precision):
     assert torch.equal(a.populations(), b.populations())
     a.close()
     b.close()
+

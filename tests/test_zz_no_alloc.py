@@ -54,3 +54,61 @@ def test_noalloc_rejects_host_memory():
     with pytest.raises(cm.CmrtError) as ei:
         cm.cmrt_diagnostics_noalloc(params, host.ctypes.data)
     assert ei.value.status == cm.CMRT_EINVAL
+
+
+def _device_pops(n=16):
+    return torch.zeros((2, 9, n, n), dtype=torch.float32, device="cuda")
+
+
+def test_noalloc_rejects_misaligned_pointer():
+    """nx a multiple of 4: the pass copies 16-byte chunks, so a base address
+    4 bytes into a tensor is refused on the host, before any launch."""
+    d, _, _ = I.static_drop(n=16, radius=4.0)
+    params = cm.make_params(d)
+    buf = torch.zeros(2 * 9 * 16 * 16 + 4, dtype=torch.float32, device="cuda")
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_diagnostics_noalloc(params, buf.data_ptr() + 4)
+    assert ei.value.status == cm.CMRT_EINVAL
+    assert "aligned" in str(ei.value)
+
+
+def test_noalloc_rejects_lattice_wider_than_scratch():
+    """983,041 columns need 8193 column strips, one more than the scratch area
+    holds: refused before the launch (the pointer is never read)."""
+    d = I.base_params(983_041, 1)
+    params = cm.make_params(d)
+    pops = _device_pops()
+    with pytest.raises(cm.CmrtError) as ei:
+        cm.cmrt_diagnostics_noalloc(params, pops.data_ptr())
+    assert ei.value.status == cm.CMRT_EINVAL
+    assert "strips" in str(ei.value)
+    # the widest accepted lattice passes the same checks (one row, 983,040 columns)
+    d = I.base_params(983_040, 1)
+    d["wall_y"] = False
+    wide = torch.zeros((2, 9, 1, 983_040), dtype=torch.float32, device="cuda")
+    wide[0, 0] = 1.0
+    wide[1, 0] = 0.1
+    out = cm.cmrt_diagnostics_noalloc(cm.make_params(d), wide.data_ptr())
+    assert out[0] == pytest.approx(983_040.0)
+    assert out[1] == pytest.approx(98_304.0)
+
+
+def test_noalloc_rejects_capturing_stream():
+    """The call waits for its stream, which a stream recording a CUDA graph
+    does not allow: it is refused with nothing enqueued, and the caller's
+    capture ends normally."""
+    d, _, _ = I.static_drop(n=16, radius=4.0)
+    params = cm.make_params(d)
+    pops = _device_pops()
+    x = torch.zeros(4, device="cuda")
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        x.add_(1.0)
+        with pytest.raises(cm.CmrtError) as ei:
+            cm.cmrt_diagnostics_noalloc(params, pops.data_ptr(), side.cuda_stream)
+    assert ei.value.status == cm.CMRT_EINVAL
+    assert "capturing" in str(ei.value)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
