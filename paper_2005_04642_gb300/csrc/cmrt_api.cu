@@ -10,12 +10,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cmrt.h"
 #include "cmrt_internal.h"
 
 using cmrt::StepParams;
 
 namespace {
+
+// NVTX range over one library call (step, fields, diagnostics, adjoint,
+// batch step), for timelines taken with a profiler attached.  NVTX v3 is
+// header-only and costs a few nanoseconds when no tool is loaded.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 thread_local std::string g_thread_error;
 
@@ -190,8 +202,8 @@ cmrt_status validate(const cmrt_params* p) {
         return fail(nullptr, CMRT_EINVAL, "ghost_N_mode must be 0 or 1");
     if (p->precision < 0 || p->precision > 2)
         return fail(nullptr, CMRT_EINVAL, "precision must be 0 (FP32), 1 (BF16) or 2 (FP16)");
-    if (p->precision_reference != 0 && p->precision_reference != 1)
-        return fail(nullptr, CMRT_EINVAL, "precision_reference must be 0 or 1");
+    if (p->precision_reference < 0 || p->precision_reference > 2)
+        return fail(nullptr, CMRT_EINVAL, "precision_reference must be 0, 1 or 2");
     if (p->adjoint_fused < 0 || p->adjoint_fused > 2)
         return fail(nullptr, CMRT_EINVAL, "adjoint_fused must be 0 (automatic), 1 (fused kernels) or 2 (plane passes)");
     if (p->diag_every < 0) return fail(nullptr, CMRT_EINVAL, "diag_every must be >= 0");
@@ -236,11 +248,32 @@ StepParams derive(const cmrt_params& p) {
     s.gvol_y = static_cast<float>(p.g_vol[1]);
     s.fixed_K = static_cast<float>(p.fixed_K);
     s.precision = p.precision;
-    // 16-bit storage keeps C_i - rho_C psi^C_i.  Reference 0: the pure-colour
-    // rest weights phi_i of Eq. eq_phi at alpha_C; reference 1: w_i.
-    // The FP32 weights are adjusted so that psi_0 + 4 psi_axis + 4 psi_diag is
-    // exactly 1 in real arithmetic: any reference decodes correctly, but one
-    // whose weights do not sum to 1 would bias colour mass every step.
+    s.precision_reference = p.precision_reference;
+    // 16-bit storage keeps C_i - rho_C psi_i.  Reference 0: phi_i of Eq. eq_phi
+    // at the node's own mixture (computed in the kernels from the stored
+    // densities with psi_axis = mix_r rho_R + mix_b rho_B over rho);
+    // reference 1: the lattice weights w_i; reference 2: phi_i of the pure
+    // colour C (alpha_C).  The constant FP32 weights are adjusted so that
+    // psi_0 + 4 psi_axis + 4 psi_diag is exactly 1 in real arithmetic: any
+    // reference decodes correctly, but one whose weights do not sum to 1 would
+    // bias colour mass every step.
+    s.mix_r = static_cast<float>((1.0 - p.alpha_r) / 5.0);
+    s.mix_b = static_cast<float>((1.0 - p.alpha_b) / 5.0);
+    // FP16 deviations are stored scaled by 2^k so that small ones stay in
+    // FP16's normal range (below 6.1e-5 it keeps only an absolute step of
+    // 6e-8, which is about 1 % of a light fluid's deviations): k = 14 for bulk
+    // densities up to 1, one less per doubling above, so that deviations up
+    // to 4 rho0 stay finite (FP16's largest value is 65504).  Scaling by a
+    // power of two commutes exactly with FP32 rounding.  BF16 has FP32's
+    // exponent range and is stored unscaled.
+    int k = 0;
+    if (p.precision == 2) {
+        const double rho_max = std::max(p.rho0_r, p.rho0_b);
+        k = 14 - std::max(0, static_cast<int>(std::ceil(std::log2(rho_max))));
+        k = std::max(k, 0);
+    }
+    s.dev_scale = static_cast<float>(std::ldexp(1.0, k));
+    s.dev_unscale = static_cast<float>(std::ldexp(1.0, -k));
     const double wts[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
     auto weights = [&](double alpha, float out[3]) {
         const double axis = p.precision_reference == 1 ? wts[1] : 1.8 * (1.0 - alpha) * wts[1];
@@ -531,6 +564,7 @@ cmrt_status cmrt_validate(const cmrt_params* p) { return validate(p); }
 
 cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0, void* cuda_stream,
                       cmrt_ctx** out) {
+    NvtxRange nvtx_range("cmrt_init");
     if (!out) return fail(nullptr, CMRT_EINVAL, "out is NULL");
     *out = nullptr;
     cmrt_status st = validate(p);
@@ -607,6 +641,7 @@ cmrt_status cmrt_init(const cmrt_params* p, const float* rho_n0, const float* u0
 }
 
 cmrt_status cmrt_step(cmrt_ctx* h, int64_t n) {
+    NvtxRange nvtx_range("cmrt_step");
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (n < 0) return fail(c, CMRT_EINVAL, "n must be >= 0");
@@ -640,6 +675,7 @@ cmrt_status cmrt_set_graph_steps(cmrt_ctx* h, int32_t steps) {
 int32_t cmrt_get_graph_steps(const cmrt_ctx* h) { return h ? h->c.graph_steps : -1; }
 
 cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, float* uy, float* p) {
+    NvtxRange nvtx_range("cmrt_fields");
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
@@ -687,6 +723,7 @@ cmrt_status cmrt_fields(cmrt_ctx* h, float* rho_r, float* rho_b, float* ux, floa
 }
 
 cmrt_status cmrt_diagnostics(cmrt_ctx* h, double out[6]) {
+    NvtxRange nvtx_range("cmrt_diagnostics");
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (!out) return fail(c, CMRT_EINVAL, "out is NULL");
@@ -1353,6 +1390,7 @@ cmrt_status cmrt_batch_init(int32_t n, const cmrt_params* params, const float* c
 }
 
 cmrt_status cmrt_batch_step(cmrt_batch* h, int64_t n) {
+    NvtxRange nvtx_range("cmrt_batch_step");
     Batch* b = blive(h);
     if (!b) return CMRT_ESTATE;
     if (n < 0) return bfail(b, CMRT_EINVAL, "n must be >= 0");
@@ -1670,6 +1708,7 @@ cmrt_status adj_zero(Ctx* c) {
 }  // namespace
 
 extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* lam, double grad_params[6]) {
+    NvtxRange nvtx_range("cmrt_step_vjp");
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (!lam_next || !lam) return fail(c, CMRT_EINVAL, "lam_next and lam must not be NULL");
@@ -1738,6 +1777,7 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out) 
 
 extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_every, const float* target, double* J,
                                     double grad_params[6], float* grad_rho_n0) {
+    NvtxRange nvtx_range("cmrt_adjoint");
     Ctx* c = live(h);
     if (!c) return CMRT_ESTATE;
     if (c->owner) return fail(c, CMRT_EINVAL, "member %d of a batch is stepped by cmrt_batch_step", c->member);

@@ -148,12 +148,26 @@ __global__ void k_unstream_in(const float* __restrict__ pre, int nx, int ny, int
 }
 
 // 16-bit storage (see cmrt_step.cu): a node keeps (rho'_R, rho'_B) in FP32 and,
-// per link, the deviations d_C,i = C_i - rho_C psi^C_i as a 16-bit pair, with
+// per link, the deviations d_C,i = C_i - rho_C psi_i as a 16-bit pair, with
 // rho_C the sum of the record's own nine populations of colour C and
 // rho'_C = rho_C - sum_i round(d_C,i), so that decoding conserves rho_C.
-__device__ __forceinline__ float psi_of(const float (&psi)[3], int i) {
-    return i == 0 ? psi[0] : ((i & 1) ? psi[2] : psi[1]);
+// The reference weights (rest, axis, diagonal) as (red, blue) pairs: the
+// node's mixture (precision_reference 0; the same exact-sum rounding as the
+// step kernel's) or per-colour constants.
+__device__ __forceinline__ void ref_weights(float rr, float rb, const StepParams& P, float2 (&w)[3]) {
+    if (P.precision_reference == 0) {
+        float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * __fdividef(1.0f, rr + rb);
+        s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
+        const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);
+        const float p0 = fmaf(-4.0f, pa, 1.0f - pa);
+        w[0] = make_float2(p0, p0);
+        w[1] = make_float2(pa, pa);
+        w[2] = make_float2(0.25f * pa, 0.25f * pa);
+    } else {
+        for (int k = 0; k < 3; ++k) w[k] = make_float2(P.psi_r[k], P.psi_b[k]);
+    }
 }
+__device__ __forceinline__ int ref_class(int i) { return i == 0 ? 0 : ((i & 1) ? 2 : 1); }
 __device__ __forceinline__ unsigned pack2(float a, float b, int precision) {
     if (precision == kPrecF16) {
         const __half2 h = __floats2half2_rn(a, b);
@@ -180,13 +194,17 @@ __global__ void k_encode(const float* __restrict__ post, StepParams P, char* __r
             rb += b[i];
         }
         unsigned* dev = reinterpret_cast<unsigned*>(state + nodes * 8);
+        float2 w[3];
+        ref_weights(rr, rb, P, w);
         float er = 0.f, eb = 0.f;  // rounded deviations, absorbed by the stored densities
+        const float S = P.dev_scale;  // a power of two: the scaled deviation is the deviation, scaled exactly
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const unsigned h = pack2(r[i] - rr * psi_of(P.psi_r, i), b[i] - rb * psi_of(P.psi_b, i), P.precision);
+            const float2 wi = w[ref_class(i)];
+            const unsigned h = pack2(fmaf(-rr * S, wi.x, r[i] * S), fmaf(-rb * S, wi.y, b[i] * S), P.precision);
             const float2 back = unpack2(h, P.precision);
-            er += back.x;
-            eb += back.y;
+            er = fmaf(back.x, P.dev_unscale, er);
+            eb = fmaf(back.y, P.dev_unscale, eb);
             dev[i * nodes + n] = h;
         }
         reinterpret_cast<float2*>(state)[n] = make_float2(rr - er, rb - eb);
@@ -199,11 +217,16 @@ __global__ void k_decode(const char* __restrict__ state, StepParams P, float* __
          n += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const float2 rho = reinterpret_cast<const float2*>(state)[n];
         const unsigned* dev = reinterpret_cast<const unsigned*>(state + nodes * 8);
+        float2 w[3];
+        ref_weights(rho.x, rho.y, P, w);
+        // the step kernel's decode: reference pair rho' psi rounded once, plus the deviation
+        float2 ref[3];
+        for (int k = 0; k < 3; ++k) ref[k] = make_float2(__fmul_rn(rho.x, w[k].x), __fmul_rn(rho.y, w[k].y));
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float2 d = unpack2(dev[i * nodes + n], P.precision);
-            post[i * nodes + n] = fmaf(rho.x, psi_of(P.psi_r, i), d.x);
-            post[(9 + i) * nodes + n] = fmaf(rho.y, psi_of(P.psi_b, i), d.y);
+            post[i * nodes + n] = __fmaf_rn(d.x, P.dev_unscale, ref[ref_class(i)].x);
+            post[(9 + i) * nodes + n] = __fmaf_rn(d.y, P.dev_unscale, ref[ref_class(i)].y);
         }
     }
 }

@@ -44,7 +44,10 @@ constexpr int kPrecF16 = 2;
 struct StepParams {
     int nx, ny, wall_y;
     int precision;                 // kPrecF32 / kPrecB16 / kPrecF16
-    float psi_r[3], psi_b[3];      // 16-bit storage reference weights (rest, axis, diagonal)
+    int precision_reference;       // 16-bit storage reference: 0 node mixture, 1 w_i, 2 pure colour
+    float psi_r[3], psi_b[3];      // constant reference weights (rest, axis, diagonal), references 1 and 2
+    float mix_r, mix_b;            // (1 - alpha_C) / 5: psi_axis of the node mixture (reference 0)
+    float dev_scale, dev_unscale;  // 16-bit deviations are stored as d * dev_scale (a power of two)
     int visc_mode, curvature_mode, ghost_N_mode;
     int stencil_order;             // 2: compact gradients; 6: App. B for grad rho^N and grad Phi'
     int adjoint_fused;              // 0: automatic, 1: fused reverse tail, 2: plane passes

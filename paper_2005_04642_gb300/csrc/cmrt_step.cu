@@ -131,6 +131,7 @@ __device__ __forceinline__ float2 sum9x2(const float (&r)[9], const float (&b)[9
 
 // 32-bit: 18 FP32 planes.
 struct LayoutF32 {
+    static constexpr bool kPrep = false;
     static constexpr int kSlotBytes = kPlanes * kWin * 4;
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
@@ -177,6 +178,7 @@ struct LayoutF32 {
         }
     };
 
+    __device__ __forceinline__ static void prep(char*, int, const StepParams&) {}
     __device__ __forceinline__ static const float* plane(const char* slot, int q) {
         return reinterpret_cast<const float*>(slot) + q * kWin;
     }
@@ -198,91 +200,126 @@ struct LayoutF32 {
     }
 };
 
-// 16-bit deviations (H = __half2 or __nv_bfloat162) from rho_C psi^C_i.
+// 16-bit deviations (H = __half2 or __nv_bfloat162) from rho_C psi_i.
+//
+// A ring row keeps, per window column, the stored densities (rho'_R, rho'_B)
+// as copied, the reference pairs (rho'_R psi^R_k, rho'_B psi^B_k) of the three
+// link classes k (rest, axis, diagonal), and the nine 16-bit deviation pairs
+// as copied.  The reference pairs are filled once per row, by the thread that
+// copied the column's densities, as soon as its copy has landed (prep); a
+// gathered population is then one packed add, reference + deviation.
 template <class H>
 struct Layout16 {
-    static constexpr int kRhoBytes = kWin * 8;  // float2 (rho_R, rho_B) per column
-    static constexpr int kDevBytes = kWin * 4;  // one 16-bit pair per column and link
-    static constexpr int kSlotBytes = kRhoBytes + 9 * kDevBytes;
-    static constexpr int kChunks = kSlotBytes / 16;
-    static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
+    static constexpr int kRhoBytes = kWin * 8;      // float2 (rho'_R, rho'_B) per column
+    static constexpr int kRefBytes = 3 * kWin * 8;  // float2 reference pair per class and column
+    static constexpr int kDevBytes = kWin * 4;      // one 16-bit pair per column and link
+    static constexpr int kDevOff = kRhoBytes + kRefBytes;
+    static constexpr int kSlotBytes = kDevOff + 9 * kDevBytes;
+    static constexpr int kDevChunks = 9 * kDevBytes / 16;
+    static constexpr int kVecIters = (kDevChunks + kThreads - 1) / kThreads;
+    static constexpr bool kPrep = true;
     static constexpr size_t node_bytes() { return 8 + 9 * 4; }
 
     __device__ __forceinline__ static float2 to2(H v);
     __device__ __forceinline__ static H from2(float a, float b);
     __device__ __forceinline__ static H from2x(float2 v) { return from2(v.x, v.y); }
 
+    // Each thread copies the densities of its own window column (8 bytes) and
+    // a share of the deviation planes (16-byte chunks of four columns, or its
+    // own column's four bytes per plane when nx is not a multiple of 4).
     template <bool VEC>
     struct Plan {
-        static constexpr int kN = VEC ? kVecIters : 10;
+        static constexpr int kN = VEC ? kVecIters : 9;
         unsigned soff[kN];
-        size_t goff[kN];     // byte offset of the chunk in row 0 of its plane
-        unsigned shift[kN];  // log2 of the element size of its plane
+        size_t goff[kN];  // byte offset of the chunk in row 0 of its plane
+        unsigned rho_soff;
+        size_t rho_goff;
         int n;
         __device__ __forceinline__ void init(int x0, int nx, size_t nodes) {
+            const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
+            rho_soff = threadIdx.x * 8;
+            rho_goff = static_cast<size_t>(gx) * 8;
             n = 0;
             if (VEC) {
-                constexpr int kRhoChunks = kRhoBytes / 16;  // 2 columns each
-                constexpr int kDevChunks = kDevBytes / 16;  // 4 columns each
+                constexpr int kPer = kDevBytes / 16;  // chunks per plane row
 #pragma unroll
                 for (int m = 0; m < kN; ++m) {
                     const int c = threadIdx.x + m * kThreads;
-                    if (c < kRhoChunks) {
-                        soff[m] = static_cast<unsigned>(c * 16);
-                        goff[m] = static_cast<size_t>(wrap(x0 - kHalo + 2 * c, nx)) * 8;
-                        shift[m] = 3;
-                    } else {
-                        const int k = c - kRhoChunks;
-                        const int p = k / kDevChunks;
-                        const int w4 = (k - p * kDevChunks) * 4;
-                        soff[m] = static_cast<unsigned>(kRhoBytes + p * kDevBytes + w4 * 4);
-                        goff[m] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 +
-                                  static_cast<size_t>(wrap(x0 - kHalo + w4, nx)) * 4;
-                        shift[m] = 2;
-                    }
-                    if (c < kChunks) n = m + 1;
+                    const int p = c / kPer;
+                    const int w4 = (c - p * kPer) * 4;
+                    soff[m] = static_cast<unsigned>(kDevOff + p * kDevBytes + w4 * 4);
+                    goff[m] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 +
+                              static_cast<size_t>(wrap(x0 - kHalo + w4, nx)) * 4;
+                    if (c < kDevChunks) n = m + 1;
                 }
             } else {
-                const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
-                soff[0] = threadIdx.x * 8;
-                goff[0] = static_cast<size_t>(gx) * 8;
-                shift[0] = 3;
 #pragma unroll
                 for (int p = 0; p < 9; ++p) {
-                    soff[1 + p] = static_cast<unsigned>(kRhoBytes + p * kDevBytes + threadIdx.x * 4);
-                    goff[1 + p] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 + static_cast<size_t>(gx) * 4;
-                    shift[1 + p] = 2;
+                    soff[p] = static_cast<unsigned>(kDevOff + p * kDevBytes + threadIdx.x * 4);
+                    goff[p] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 + static_cast<size_t>(gx) * 4;
                 }
                 n = kN;
             }
         }
         __device__ __forceinline__ void issue(unsigned slot_addr, const char* state, int gy, int nx) const {
             const size_t row_nodes = static_cast<size_t>(gy) * nx;
+            cp_async8(slot_addr + rho_soff, state + rho_goff + row_nodes * 8);
 #pragma unroll
             for (int m = 0; m < kN; ++m) {
                 if (m < n) {
-                    const char* g = state + goff[m] + (row_nodes << shift[m]);
+                    const char* g = state + goff[m] + row_nodes * 4;
                     if (VEC) cp_async16(slot_addr + soff[m], g);
-                    else if (m == 0) cp_async8(slot_addr + soff[m], g);
                     else cp_async4(slot_addr + soff[m], g);
                 }
             }
         }
     };
 
-    // reference weight psi^C_i of link i: rest, axis or diagonal class
-    __device__ __forceinline__ static float psi_r(int i, const StepParams& P) {
-        return i == 0 ? P.psi_r[0] : ((i & 1) ? P.psi_r[2] : P.psi_r[1]);
+    // Reference weights (psi_rest, psi_axis, psi_diag) of a node, as (red, blue)
+    // pairs.  precision_reference 0: phi_i of Eq. eq_phi at the node's own
+    // mixture, psi_axis = ((1 - alpha_R) rho_R + (1 - alpha_B) rho_B) / (5 rho)
+    // rounded to a multiple of 2^-24, psi_diag = psi_axis / 4 and psi_rest =
+    // 1 - 5 psi_axis: all three exact in FP32, so psi_rest + 4 psi_axis + 4
+    // psi_diag = 1 exactly and decoding conserves each colour's mass.  Other
+    // references: per-colour constants (psi_r, psi_b).
+    __device__ __forceinline__ static void weights(float rr, float rb, float inv_rho, const StepParams& P,
+                                                   float2& w0, float2& wa, float2& wd) {
+        if (P.precision_reference == 0) {
+            float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * inv_rho;
+            s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
+            const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);  // a multiple of 2^-24
+            const float p0 = fmaf(-4.0f, pa, 1.0f - pa);              // 1 - 5 pa, exact
+            w0 = make_float2(p0, p0);
+            wa = make_float2(pa, pa);
+            wd = make_float2(0.25f * pa, 0.25f * pa);
+        } else {
+            w0 = make_float2(P.psi_r[0], P.psi_b[0]);
+            wa = make_float2(P.psi_r[1], P.psi_b[1]);
+            wd = make_float2(P.psi_r[2], P.psi_b[2]);
+        }
     }
-    __device__ __forceinline__ static float psi_b(int i, const StepParams& P) {
-        return i == 0 ? P.psi_b[0] : ((i & 1) ? P.psi_b[2] : P.psi_b[1]);
+
+    // Reference pairs of window column t of a ring row whose copy has landed
+    // (the calling thread copied that column's densities itself).
+    __device__ __forceinline__ static void prep(char* slot, int t, const StepParams& P) {
+        const float2 rho = reinterpret_cast<const float2*>(slot)[t];
+        float2 w0, wa, wd;
+        weights(rho.x, rho.y, rcp(rho.x + rho.y), P, w0, wa, wd);
+        float2* ref = reinterpret_cast<float2*>(slot + kRhoBytes);
+        ref[t] = __fmul2_rn(rho, w0);
+        ref[kWin + t] = __fmul2_rn(rho, wa);
+        ref[2 * kWin + t] = __fmul2_rn(rho, wd);
     }
+
+    // link class of link i: rest 0, axis 1 (even i), diagonal 2 (odd i)
+    __device__ __forceinline__ static constexpr int cls(int i) { return i == 0 ? 0 : ((i & 1) ? 2 : 1); }
     __device__ __forceinline__ static void pair(const char* slot, int i, int col, const StepParams& P, float& r,
                                                 float& b) {
-        const float2 rho = reinterpret_cast<const float2*>(slot)[col];
-        const H d = reinterpret_cast<const H*>(slot + kRhoBytes + i * kDevBytes)[col];
+        const float2 ref = reinterpret_cast<const float2*>(slot + kRhoBytes)[cls(i) * kWin + col];
+        const H d = reinterpret_cast<const H*>(slot + kDevOff + i * kDevBytes)[col];
         // (R_i, B_i) = (rho'_R psi^R_i, rho'_B psi^B_i) + d_i as one packed FP32x2 FMA
-        const float2 c = __ffma2_rn(rho, make_float2(psi_r(i, P), psi_b(i, P)), to2(d));
+        // (the stored deviation times 2^-k, exact, plus the reference, rounded once)
+        const float2 c = __ffma2_rn(to2(d), make_float2(P.dev_unscale, P.dev_unscale), ref);
         r = c.x;
         b = c.y;
     }
@@ -290,22 +327,28 @@ struct Layout16 {
     __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
                                                  float rr, float rb, float inv_rho, float sx, float sy,
                                                  const StepParams& P) {
+        // everything scaled by 2^k (dev_scale) before rounding to 16 bits: a
+        // power-of-two factor commutes exactly with every FP32 operation below
+        const float S = P.dev_scale;
         float seg[9];
-        segregation(sx, sy, seg);
+        segregation(sx * S, sy * S, seg);
         H* dev = reinterpret_cast<H*>(dst + nodes * 8) + node;
         const float aR = rr * inv_rho, aB = rb * inv_rho;
+        float2 w[3];
+        weights(rr, rb, inv_rho, P, w[0], w[1], w[2]);
         // the stored densities absorb the rounding of the deviations, so that the
         // decoded populations of the record sum to rho_R and rho_B (colour mass is
         // conserved as with FP32 storage): rho'_C = rho_C - sum_i round(d_C,i)
         // packed FP32x2 arithmetic on the (red, blue) pair of each link, lane by
         // lane the same roundings as the scalar form
         float2 e = make_float2(0.0f, 0.0f);
-        const float2 a2 = make_float2(aR, aB), mrho = make_float2(-rr, -rb);
+        const float2 a2 = make_float2(aR * S, aB * S), mrho = make_float2(-rr * S, -rb * S);
+        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float2 C = __ffma2_rn(a2, make_float2(fp[i], fp[i]), make_float2(seg[i], -seg[i]));
-            const H h = from2x(__ffma2_rn(mrho, make_float2(psi_r(i, P), psi_b(i, P)), C));
-            e = __fadd2_rn(e, to2(h));
+            const H h = from2x(__ffma2_rn(mrho, w[cls(i)], C));
+            e = __ffma2_rn(to2(h), un2, e);
             dev[i * nodes] = h;
         }
         reinterpret_cast<float2*>(dst)[node] = make_float2(rr - e.x, rb - e.y);
@@ -674,6 +717,7 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
         for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
             const int s = s_first + k;
             cp_wait<1>();
+            if (L::kPrep && s <= s_last && row_ok(s)) L::prep(R.pop + ks * L::kSlotBytes, t, P);
             __syncthreads();
             if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2, ring_next(ring_next(ks)));
             cp_commit();
@@ -692,6 +736,8 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
         for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
             const int s = s_first + k;
             cp_wait<1>();
+            // row s has landed: this thread's column of it gets its reference pairs
+            if (L::kPrep && s <= s_last && row_ok(s)) L::prep(R.pop + ks * L::kSlotBytes, t, P);
             bar_sync<kBarFront, kThreads>();
             // row s + 2 goes to the slot of row s - 7, last read by D of iteration k - 2
             if (s + 2 <= s_last && row_ok(s + 2)) issue_row(s + 2, ring_next(ring_next(ks)));

@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(cm):
 
 
 def test_abi_version_and_struct_size(cm):
-    assert cm.cmrt_abi_version() == 7
+    assert cm.cmrt_abi_version() == 8
     assert cm.load().cmrt_params_size() == ctypes.sizeof(cm.cmrt_params)
 
 
@@ -57,7 +57,7 @@ def test_defaults_are_valid(cm):
     ("sigma", -1.0, "sigma"),
     ("stencil_order", 4, "stencil_order"),
     ("precision", 3, "precision"),
-    ("precision_reference", 2, "precision_reference"),
+    ("precision_reference", 3, "precision_reference"),
     ("adjoint_fused", 3, "adjoint_fused"),
     ("visc_mode", 3, "visc_mode"),
     ("wall_y", 2, "wall_y"),
