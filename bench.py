@@ -581,6 +581,24 @@ def run_adjoint_only(args):
                       "J": J}), flush=True)
 
 
+def run_profile_step(args):
+    """Only the device-resident steps of the drops field of --side in storage
+    form --precision (init, --warmup steps, --steps steps): a short command
+    for ncu captures of the step kernel.  Prints one JSON line."""
+    import torch
+    from paper_2005_04642_gb300 import cmrt as cm
+    cm.load()
+    d, rn, u = make_workload(args.side)
+    d = dict(d, precision=args.precision)
+    stream = torch.cuda.current_stream()
+    ms, diag = time_steps(cm, d, rn, u, args.steps, args.warmup, stream)
+    cells = d["nx"] * d["ny"]
+    nbytes = 144 if args.precision == 0 else 88
+    print(json.dumps({"side": args.side, "precision": args.precision, "ms_per_step": ms,
+                      "MLUPS": cells / (ms * 1e-3) / 1e6, "GBs": nbytes * cells / (ms * 1e-3) / 1e9,
+                      "nonfinite": diag["nonfinite"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,9 +614,18 @@ def main():
                     help="time only cmrt_adjoint on the drops field of --side (--steps steps, checkpoints every "
                          "--ckpt-every); a short run for launch lists of the reverse passes")
     ap.add_argument("--ckpt-every", type=int, default=10)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="time only the steps of the drops field of --side in storage form --precision "
+                         "(a short run for ncu captures of the step kernel)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="storage form for --profile-step: 0 FP32, 1 BF16, 2 FP16")
     args = ap.parse_args()
     if args.adjoint_only:
         run_adjoint_only(args)
+        return
+    if args.profile_step:
+        args.warmup = max(args.warmup, 3)
+        run_profile_step(args)
         return
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -168,3 +168,34 @@ def layered_transient(rho_nodes, eta_nodes, u_init_nodes, t, refine=2):
     uf = (V @ w) * s
     # average the fine cells back onto the nodes
     return uf.reshape(H, refine).mean(axis=1)
+
+
+def app_d_steady(rho_nodes, nu, G, samples_per_half_lu=200):
+    """App. D, Eq. equ_integral: steady pressure-driven flow through the
+    symmetric stratified channel (walls at y = -1/2 and H - 1/2, profile
+    symmetric about the channel centre):
+
+        u(x) = G / (2 nu) * int_0^x (H - 2a) / rho(a) da,   x <= H/2,
+
+    mirrored about H/2, with x = y + 1/2 the distance from the wall.  The sign
+    is taken so that the flow follows the force (the printed form has
+    d/dx(eta du/dx) = +G with the pressure gradient -G).  rho is interpolated
+    linearly between nodes and held constant over the half cell next to each
+    wall; the integral is evaluated by the composite Simpson rule, as App. D
+    does, on a grid of 2 * samples_per_half_lu intervals per lattice unit.
+    Returns u at the nodes."""
+    rho_nodes = np.asarray(rho_nodes, dtype=np.float64)
+    H = rho_nodes.size
+    m = 2 * int(samples_per_half_lu)            # intervals per lattice unit (even)
+    x = np.linspace(0.0, H / 2.0, H * m // 2 + 1)
+    rho = np.interp(x - 0.5, np.arange(H, dtype=np.float64), rho_nodes)
+    f = (H - 2.0 * x) / rho
+    h = x[1] - x[0]
+    # cumulative composite Simpson rule at every even grid point
+    pair = h / 3.0 * (f[:-2:2] + 4.0 * f[1:-1:2] + f[2::2])
+    I = np.concatenate([[0.0], np.cumsum(pair)])
+    xe = x[::2]
+    half = G / (2.0 * nu) * I
+    s = np.arange(H, dtype=np.float64) + 0.5
+    d = np.minimum(s, H - s)                   # distance to the nearer wall
+    return np.interp(d, xe, half)

@@ -179,3 +179,44 @@ def batch_ensemble(n=512, seed=5, sides=BATCH_SIDES):
         rho_n = drops_field(s, s, [(s / 2.0, s / 2.0)], [s / 4.0], dtype=np.float32)
         members.append((p, rho_n, None))
     return members
+
+
+def ba_channel(H=200, nx=4, nu=0.333, G=1e-8, width=2.0, beta=0.67, stencil_order=6):
+    """Steady stratified channel flow of Sec. 4 (the Ba test, App. D).
+
+    Walls at y = -1/2 and H - 1/2 (H = L_x = 200 in the paper), the heavy (red)
+    fluid in the middle half and the light (blue) fluid next to both walls,
+    interfaces at H/4 and 3H/4 from the wall; alpha_B = 0.2, alpha_R = 0.9,
+    so Lambda = (1 - alpha_B) / (1 - alpha_R) = 8; both fluids nu = 0.333; a
+    uniform force per unit volume G along x stands for the pressure gradient.
+    The flow is invariant along x, so a few columns carry it.  The paper
+    computes the colour gradient with App. B's stencil here.  beta (the
+    recolour parameter) is not printed for this test: 0.67 as elsewhere."""
+    p = base_params(nx, H, rho0_r=1.0, rho0_b=0.125, sigma=0.005, beta=beta, wall_y=True,
+                    lambda3_r=lambda3_for_nu(nu), lambda3_b=lambda3_for_nu(nu), g_vol=(G, 0.0),
+                    stencil_order=stencil_order)
+    p["alpha_r"], p["alpha_b"] = 0.9, 0.2
+    y = np.arange(H, dtype=np.float64)
+    lo, hi = H / 4.0 - 0.5, 3.0 * H / 4.0 - 0.5  # node coordinates of the two interfaces
+    prof = np.where(y < (H - 1) / 2.0, np.tanh((y - lo) / width), np.tanh((hi - y) / width))
+    rho_n = np.broadcast_to(prof[:, None], (H, nx)).copy()
+    return p, rho_n, np.zeros((2, H, nx))
+
+
+MICRO_CURRENT_LAMBDAS = (0.001, 0.01, 0.1, 10.0, 100.0, 1000.0)
+
+
+def micro_current_drop(Lambda, n=200, radius=60.0, fixed_K=False, sigma=0.005, beta=0.67, nu=1.0 / 6.0):
+    """Static red drop of Sec. 4.2 (the micro-current study): radius 60,
+    centred in a 200 x 200 periodic box, at rest.  Lambda = rho0_R / rho0_B
+    with the larger density 1; alpha as in the paper's tables (the lighter
+    fluid 0.5).  fixed_K replaces the computed curvature by K = 1/R.  The
+    paper prints neither sigma, beta nor nu for this study: 0.005, 0.67 and
+    1/6 as in the static-drop workload."""
+    rho0_r, rho0_b = (1.0, 1.0 / Lambda) if Lambda >= 1.0 else (Lambda, 1.0)
+    p = base_params(n, n, rho0_r=rho0_r, rho0_b=rho0_b, sigma=sigma, beta=beta,
+                    lambda3_r=lambda3_for_nu(nu), lambda3_b=lambda3_for_nu(nu))
+    if fixed_K:
+        p["curvature_mode"], p["fixed_K"] = 1, 1.0 / radius
+    rho_n = drops_field(n, n, [(n / 2.0, n / 2.0)], [radius])
+    return p, rho_n, np.zeros((2, n, n))

@@ -283,3 +283,17 @@ def test_fp32_storage_floor_within_parity_bar():
     uref = max(np.abs(np.stack([f64["ux"], f64["uy"]])).max(), 0.01)
     for k in ("ux", "uy"):
         assert np.abs(f32[k] - f64[k]).max() / uref < 1e-5
+
+
+def test_app_d_simpson_solution():
+    """App. D's Simpson-rule solution of the stratified channel (Eq.
+    equ_integral) reduces to plane Poiseuille flow for a uniform density and
+    agrees with the independent trapezoid integration of the general steady
+    problem for the symmetric three-layer profile of the Ba test."""
+    H, nu, G = 200, 0.333, 1e-8
+    u = A.app_d_steady(np.full(H, 0.5), nu, G)
+    np.testing.assert_allclose(u, A.poiseuille(H, G, 0.5 * nu), rtol=1e-12)
+    _, rn, _ = I.ba_channel(H=H)
+    rho = 1.0 * (1 + rn[:, 0]) / 2 + 0.125 * (1 - rn[:, 0]) / 2
+    ref = A.layered_steady(rho, np.full(H, nu), g_vol=G)
+    np.testing.assert_allclose(A.app_d_steady(rho, nu, G), ref, rtol=1e-6)
