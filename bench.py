@@ -91,6 +91,97 @@ def recorded_traffic(cells):
 
 
 # ---------------------------------------------------------------- clocks
+class NvmlClockSampler:
+    """SM clock and clock-event reasons of the GPU in use, read through NVML
+    (read-only queries) every few milliseconds in a background thread during
+    the timed region; the device is found by its PCI bus id, so that the
+    sample is of the GPU the process runs on whatever the device numbering."""
+
+    # clock-event reason bits of NVML's public API
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index, period_s=0.005):
+        self.cuda_index = cuda_index
+        self.period = period_s
+        self.samples = []
+        self.max_mhz = None
+        self.ok = False
+
+    def __enter__(self):
+        import ctypes
+        import threading
+        import torch
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return self
+            props = torch.cuda.get_device_properties(self.cuda_index)
+            bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0".encode()
+            self.dev = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.dev)) != 0:
+                return self
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx)) == 0:  # 1: SM clock
+                self.max_mhz = float(mx.value)
+            self.reasons_fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.ok = True
+            self.thread.start()
+        except Exception:
+            self.ok = False
+        return self
+
+    def _run(self):
+        import ctypes
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            if (self.nvml.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk)) == 0 and
+                    self.reasons_fn(self.dev, ctypes.byref(rs)) == 0):
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self.stop.set()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
+
+
+class Clocks:
+    """NVML sampling where the library loads, else nvidia-smi."""
+
+    def __init__(self, gpu_index):
+        self.nvml = NvmlClockSampler(gpu_index)
+        self.smi = ClockSampler(gpu_index)
+
+    def __enter__(self):
+        self.nvml.__enter__()
+        if not self.nvml.ok:
+            self.smi.__enter__()
+        return self
+
+    def __exit__(self, *exc):
+        self.nvml.__exit__(*exc)
+        if not self.nvml.ok:
+            self.smi.__exit__(*exc)
+
+    def summary(self):
+        return self.nvml.summary() or self.smi.summary()
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -290,7 +381,7 @@ def run_cmrt(args, rank, world, local_rank):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_launch0 = lat.launches
-    with ClockSampler(local_rank) as clk:
+    with Clocks(local_rank) as clk:
         barrier()
         ev0.record(stream)
         lat.step(args.steps)
