@@ -63,6 +63,11 @@ struct Ctx {
     size_t adj_ckpt_cap = 0;
     float* adj_seg = nullptr;            // segment states (slot 0: the checkpoint), float[cap][18][n]
     size_t adj_seg_cap = 0;
+    // forward fields of segment states 0 .. cap - 1, written by the replayed
+    // steps for the reverse steps, float[cap][kFwdPlanes][n]; null where the
+    // reverse step recomputes them (plane passes, or no memory for them)
+    float* adj_fields = nullptr;
+    size_t adj_fields_cap = 0;
     // CUDA graphs of one checkpoint segment (replay + reverse steps), keyed by
     // the segment length and the adjoint buffer it starts from; recorded on a
     // private stream and valid while the workspace pointers stay put
@@ -70,6 +75,7 @@ struct Ctx {
         int64_t len;
         int a;
         cudaGraphExec_t exec;
+        int64_t launches;  // kernels one replay of the graph launches
     };
     std::vector<AdjGraph> adj_graphs;
     cudaStream_t adj_capture = nullptr;  // private stream on which graphs are recorded
@@ -391,8 +397,9 @@ void free_all(Ctx* c) {
         if (l) cudaFree(l), l = nullptr;
     if (c->adj_ckpt) cudaFree(c->adj_ckpt), c->adj_ckpt = nullptr;
     if (c->adj_seg) cudaFree(c->adj_seg), c->adj_seg = nullptr;
+    if (c->adj_fields) cudaFree(c->adj_fields), c->adj_fields = nullptr;
     c->adj_bytes = 0;
-    c->adj_ckpt_cap = c->adj_seg_cap = 0;
+    c->adj_ckpt_cap = c->adj_seg_cap = c->adj_fields_cap = 0;
     drop_adj_graphs(c);
     drop_step_graphs(c);
     if (c->adj_capture) cudaStreamDestroy(c->adj_capture), c->adj_capture = nullptr;
@@ -1686,6 +1693,24 @@ cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
         if ((st = grow(reinterpret_cast<void**>(&c->adj_seg), seg * state))) return st;
         c->adj_seg_cap = seg;
     }
+    // Forward fields of the segment states the replay passes through (all
+    // but the last), where the reverse step runs fused.  Optional: without
+    // the memory for them the reverse steps recompute the fields.
+    const size_t nfields = cmrt::adj_fused(c->sp) && seg > 1 ? seg - 1 : 0;
+    if (nfields > c->adj_fields_cap) {
+        const size_t fstate = static_cast<size_t>(cmrt::kFwdPlanes) * n * sizeof(float);
+        CK(c, cudaStreamSynchronize(c->stream));
+        drop_adj_graphs(c);  // they name the old buffer, or none
+        if (c->adj_fields) cudaFree(c->adj_fields), c->adj_fields = nullptr, c->adj_bytes -= c->adj_fields_cap * fstate;
+        c->adj_fields_cap = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&c->adj_fields), nfields * fstate) == cudaSuccess) {
+            c->adj_fields_cap = nfields;
+            c->adj_bytes += nfields * fstate;
+        } else {
+            cudaGetLastError();  // not an error: the reverse steps recompute the fields
+            c->adj_fields = nullptr;
+        }
+    }
     return CMRT_OK;
 }
 
@@ -1741,14 +1766,24 @@ extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* 
 // The graph of one checkpoint segment of `len` steps whose reverse sweep
 // starts from adjoint buffer `a`: recompute the states 1 .. len - 1 of the
 // segment buffer from slot 0 (the checkpoint), then the reverse steps
-// len - 1 .. 0.  Recorded on the first use of (len, a) -- on a private
-// stream, so the caller's stream may be any -- and replayed afterwards.
-cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out) {
+// len - 1 .. 0.  Where the reverse step runs fused and the field buffer is
+// there, the step that recomputes state j + 1 also writes the forward fields
+// of state j, bit for bit those the reverse step would recompute, so that
+// reverse steps len - 2 .. 0 skip that recomputation.  Recorded on the first
+// use of (len, a) -- on a private stream, so the caller's stream may be any
+// -- and replayed afterwards; *launches receives its kernel count.
+cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out, int64_t* launches) {
     for (const Ctx::AdjGraph& g : c->adj_graphs)
         if (g.len == len && g.a == a) {
             *out = g.exec;
+            *launches = g.launches;
             return CMRT_OK;
         }
+    const bool emit = c->adj_fields && cmrt::adj_fused(c->sp) && len > 1 &&
+                      static_cast<size_t>(len - 1) <= c->adj_fields_cap;
+    const size_t nf = static_cast<size_t>(cmrt::kFwdPlanes) * cells(*c);
+    auto fields = [&](int64_t j) { return c->adj_fields + static_cast<size_t>(j) * nf; };
+    int64_t count = 0;
     if (!c->adj_capture) CK(c, cudaStreamCreateWithFlags(&c->adj_capture, cudaStreamNonBlocking));
     const size_t n18 = 18 * cells(*c);
     auto slot = [&](int64_t j) { return c->adj_seg + static_cast<size_t>(j) * n18; };
@@ -1757,11 +1792,22 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out) 
     cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->adj_capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int64_t j = 1; j < len && e == cudaSuccess; ++j) step_once(c, slot(j - 1), slot(j), &e);
+        for (int64_t j = 1; j < len && e == cudaSuccess; ++j) {
+            if (emit) {
+                e = cmrt::launch_step_fields(slot(j - 1), slot(j), c->sp, c->rows, c->d_flag, fields(j - 1),
+                                             c->stream);
+                count += 1;
+            } else {
+                count += step_once(c, slot(j - 1), slot(j), &e);
+            }
+        }
         int aa = a;
-        for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j, aa ^= 1)
+        for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j, aa ^= 1) {
+            const float* fwd = emit && j < len - 1 ? fields(j) : nullptr;
             e = cmrt::launch_adjoint_step(slot(j), c->adj_lam[aa], c->sp, c->adj_scratch, c->adj_partials,
-                                          c->adj_lam[aa ^ 1], c->stream);
+                                          c->adj_lam[aa ^ 1], c->stream, fwd);
+            count += cmrt::adj_launches_per_step(c->sp) - (fwd ? 1 : 0);
+        }
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(c->adj_capture, &g);
         if (e == cudaSuccess) e = e2;
@@ -1770,8 +1816,9 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out) 
     }
     c->stream = user;
     if (e != cudaSuccess) return fail(c, CMRT_ECUDA, "recording the adjoint segment graph failed: %s", cudaGetErrorString(e));
-    c->adj_graphs.push_back({len, a, exec});
+    c->adj_graphs.push_back({len, a, exec, count});
     *out = exec;
+    *launches = count;
     return CMRT_OK;
 }
 
@@ -1832,7 +1879,6 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     // Otherwise segments in reverse: the checkpoint goes to slot 0 of the
     // segment buffer, then one graph recomputes the segment's states from it
     // and runs its reverse steps
-    const int per_step = c->p.stencil_order == 6 ? 4 : 1;
     if (K == 1) {
         for (int64_t t = nsteps - 1; t >= 0; --t, a ^= 1)
             CK(c, cmrt::launch_adjoint_step(c->adj_ckpt + static_cast<size_t>(t) * n18, c->adj_lam[a], c->sp,
@@ -1844,9 +1890,10 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
         CK(c, cudaMemcpyAsync(c->adj_seg, c->adj_ckpt + static_cast<size_t>(k) * n18, state, cudaMemcpyDeviceToDevice,
                               c->stream));
         cudaGraphExec_t exec = nullptr;
-        if ((st = adj_segment_graph(c, len, a, &exec)) != CMRT_OK) return st;
+        int64_t nl = 0;
+        if ((st = adj_segment_graph(c, len, a, &exec, &nl)) != CMRT_OK) return st;
         CK(c, cudaGraphLaunch(exec, c->stream));
-        c->launches += (len - 1) * per_step + len * cmrt::adj_launches_per_step(c->sp);
+        c->launches += nl;
         a ^= static_cast<int>(len & 1);
     }
     if (grad_rho_n0) {

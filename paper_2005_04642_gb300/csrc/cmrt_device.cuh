@@ -67,11 +67,12 @@ __host__ __device__ constexpr float chy(int i) {
 // Compact isotropic first derivative (Sec. 2; App. B with N = 1):
 //   d_a X = 3 sum_i w_i X(r + c_i) c_ia
 // written out: axis neighbours carry 1/3, diagonals 1/12.
+// (the multiply-add written out, so that every kernel rounds it alike)
 __device__ __forceinline__ float ddx(float e, float w, float ne, float nw, float se, float sw) {
-    return (1.0f / 3.0f) * (e - w) + (1.0f / 12.0f) * ((ne - nw) + (se - sw));
+    return fmaf(1.0f / 3.0f, e - w, (1.0f / 12.0f) * ((ne - nw) + (se - sw)));
 }
 __device__ __forceinline__ float ddy(float n, float s, float ne, float nw, float se, float sw) {
-    return (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * ((ne - se) + (nw - sw));
+    return fmaf(1.0f / 3.0f, n - s, (1.0f / 12.0f) * ((ne - se) + (nw - sw)));
 }
 
 // Guard of the unit normal n-hat = -grad rho^N / |grad rho^N| (Sec. 2), which

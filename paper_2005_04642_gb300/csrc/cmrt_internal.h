@@ -64,13 +64,25 @@ struct StepParams {
     float fixed_K;
 };
 
-// Output buffers of the field pass (any may be null).
+// Output buffers of the field pass (any may be null); `fwd` receives the
+// forward fields of a step's input state (Pass::StepFields), kFwdPlanes planes
+// float[kFwdPlanes][ny][nx] in the order of FwdPlane.
 struct FieldOut {
     float* rho_r;
     float* rho_b;
     float* ux;
     float* uy;
     float* p;
+    float* fwd;
+};
+
+// The forward fields of a state that one reverse step of the adjoint reads,
+// as planes: colour densities, momentum, colour fractions, Phi', grad rho^N,
+// K, the force G and the force-adjusted velocity u (the first planes of the
+// adjoint's scratch, and the layout Pass::StepFields writes).
+enum FwdPlane : int {
+    kFwdRR = 0, kFwdRB, kFwdJX, kFwdJY, kFwdCHR, kFwdCHB, kFwdPHIP, kFwdGX, kFwdGY, kFwdK, kFwdGFX, kFwdGFY, kFwdUX,
+    kFwdUY, kFwdPlanes
 };
 
 // Geometry of the fused row-marching kernel: a CTA owns a strip of kTileX
@@ -83,7 +95,9 @@ constexpr int kHalo = 4;
 constexpr int kTileX = kWin - 2 * kHalo;  // 120
 constexpr int kRing = 9;                  // rows of post-collision populations kept in shared memory
 
-enum class Pass : int { Step = 0, Fields = 1, Diag = 2 };
+// Step: one time step; StepFields: the same step, also writing the forward
+// fields of its input state (FP32 storage, for the adjoint's segment replay).
+enum class Pass : int { Step = 0, Fields = 1, Diag = 2, StepFields = 3 };
 
 // Number of FP64 partial sums each CTA of the diagnostics pass writes.
 constexpr int kDiagSlots = 6;  // mass_r, mass_b, mom_x, mom_y, max|u|^2, non-finite count
@@ -99,6 +113,11 @@ int chain_rows(int nx, int ny, int sms, int precision);
 // P.precision, dst receives P_t.  flag is set non-zero if a node has a
 // non-finite density.
 cudaError_t launch_step(const void* src, void* dst, const StepParams& P, int rows, unsigned* flag, cudaStream_t s);
+// The same step (FP32 storage, compact stencil) also writing the forward
+// fields of src (the state P_{t-1}) into fwd[kFwdPlanes][ny][nx], bit for bit
+// the values the adjoint's own forward recomputation gives.
+cudaError_t launch_step_fields(const float* src, float* dst, const StepParams& P, int rows, unsigned* flag,
+                               float* fwd, cudaStream_t s);
 // Fields of the state whose post-collision populations are in src.
 cudaError_t launch_fields(const void* src, const StepParams& P, int rows, FieldOut out, cudaStream_t s);
 // Per-CTA FP64 partial diagnostics into partials[grid][kDiagSlots].
@@ -152,9 +171,13 @@ constexpr int kAdjPlanes = 38;
 constexpr int kAdjSlots = 8;
 int adj_blocks(int nx, int ny);
 int adj_launches_per_step(const StepParams& P);
-// lam_post: adjoint of P_t; post: P_{t-1}; writes the adjoint of P_{t-1} into lam_prev
+// lam_post: adjoint of P_t; post: P_{t-1}; writes the adjoint of P_{t-1} into lam_prev.
+// fwd: the forward fields of post written by launch_step_fields, or null to
+// recompute them (used only where adj_fused(P)).
 cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
-                                double* partials, float* lam_prev, cudaStream_t s);
+                                double* partials, float* lam_prev, cudaStream_t s, const float* fwd = nullptr);
+// whether one reverse step runs as the fused kernels (compact stencil, lattice large enough or asked for)
+bool adj_fused(const StepParams& P);
 // same, but writes dJ/df(t) (pre-collision, float[2][9][ny][nx]) into lam_pre
 cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                     double* partials, float* lam_pre, cudaStream_t s);

@@ -55,6 +55,10 @@ enum Plane : int {
     kNumPlanes
 };
 static_assert(kNumPlanes == kAdjPlanes, "scratch plane count");
+static_assert(kRR == kFwdRR && kRB == kFwdRB && kCHR == kFwdCHR && kCHB == kFwdCHB && kPHIP == kFwdPHIP &&
+                  kGX == kFwdGX && kGY == kFwdGY && kK == kFwdK && kGFX == kFwdGFX && kGFY == kFwdGFY &&
+                  kUX == kFwdUX && kUY == kFwdUY && kFB0 == kFwdPlanes,
+              "the forward planes lead the scratch planes, in the order the step kernel writes them");
 
 // periodic image of v in [0, n); the integer modulo only for images more than
 // one period away (lattices narrower than a stencil's reach)
@@ -531,10 +535,12 @@ __device__ __forceinline__ void store_rev_collide(float* __restrict__ S, size_t 
 }
 
 // The reverse collision pass: lam is the adjoint of the post-collision state P_t (18 planes).
+// F: the forward planes of post (the first kFwdPlanes planes of S, or those a
+// replayed step wrote); S: the adjoint's scratch planes.
 template <int ORDER, bool W>
 __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ post, const float* __restrict__ lam,
-                                                      const StepParams P, float* __restrict__ S,
-                                                      double* __restrict__ partials) {
+                                                      const StepParams P, const float* __restrict__ F,
+                                                      float* __restrict__ S, double* __restrict__ partials) {
     const int x = blockIdx.x * kAT + threadIdx.x, y = blockIdx.y;
     float acc[3] = {0.0f, 0.0f, 0.0f};  // beta, lambda3_r, lambda3_b
     if (x < P.nx) {
@@ -545,9 +551,9 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
         float dPx, dPy, dux, duy, t0, t1;
-        L.template grad<ORDER>(S + kPHIP * L.n, 1.0f, dPx, dPy);
-        L.template grad<2>(S + kUX * L.n, -1.0f, dux, t0);
-        L.template grad<2>(S + kUY * L.n, -1.0f, t1, duy);
+        L.template grad<ORDER>(F + kPHIP * L.n, 1.0f, dPx, dPy);
+        L.template grad<2>(F + kUX * L.n, -1.0f, dux, t0);
+        L.template grad<2>(F + kUY * L.n, -1.0f, t1, duy);
         float lr[9], lb[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -555,9 +561,9 @@ __global__ void __launch_bounds__(kAT) k_rev_collide(const float* __restrict__ p
             lb[i] = lam[static_cast<size_t>(9 + i) * L.n + o];
         }
         RevCollide r;
-        rev_collide_node(f, S[kRR * L.n + o], S[kRB * L.n + o], S[kUX * L.n + o], S[kUY * L.n + o],
-                         S[kGFX * L.n + o], S[kGFY * L.n + o], S[kGX * L.n + o], S[kGY * L.n + o],
-                         S[kCHR * L.n + o] - S[kCHB * L.n + o], dPx, dPy, dux + duy, lr, lb, P, r);
+        rev_collide_node(f, F[kRR * L.n + o], F[kRB * L.n + o], F[kUX * L.n + o], F[kUY * L.n + o],
+                         F[kGFX * L.n + o], F[kGFY * L.n + o], F[kGX * L.n + o], F[kGY * L.n + o],
+                         F[kCHR * L.n + o] - F[kCHB * L.n + o], dPx, dPy, dux + duy, lr, lb, P, r);
         store_rev_collide(S, L.n, o, r);
 #pragma unroll
         for (int j = 0; j < 3; ++j) acc[j] = r.acc[j];
@@ -720,9 +726,9 @@ template <int M>
 __device__ __forceinline__ int tail_slot(int r) { return static_cast<int>(static_cast<unsigned>(r + 64 * M) % M); }
 
 template <bool W, bool EXPAND>
-__global__ void __launch_bounds__(kWin, 5) k_rev_tail(const StepParams P, const float* __restrict__ S,
-                                                   float* __restrict__ lam, const int rows,
-                                                   double* __restrict__ partials) {
+__global__ void __launch_bounds__(kWin, 5) k_rev_tail(const StepParams P, const float* __restrict__ F,
+                                                   const float* __restrict__ S, float* __restrict__ lam,
+                                                   const int rows, double* __restrict__ partials) {
     extern __shared__ __align__(16) float tsm[];
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny;
@@ -774,7 +780,10 @@ __global__ void __launch_bounds__(kWin, 5) k_rev_tail(const StepParams P, const 
         if (in_R2(s - 1)) {
             const size_t o = node(s - 1);
 #pragma unroll
-            for (int j = 0; j < 17; ++j) in2_next[j] = S[static_cast<size_t>(kIn2[j]) * n + o];
+            for (int j = 0; j < 17; ++j) {
+                const int pl = kIn2[j];
+                in2_next[j] = (pl < kFwdPlanes ? F : S)[static_cast<size_t>(pl) * n + o];
+            }
         }
         if (in_R4(s - 3)) {
             const size_t o = node(s - 3);
@@ -943,7 +952,8 @@ bool use_fused(const StepParams& P) {
 }
 
 template <bool W, bool EXPAND>
-cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double* partials, cudaStream_t s) {
+cudaError_t launch_tail(const StepParams& P, const float* F, const float* S, float* lam, double* partials,
+                        cudaStream_t s) {
     static std::atomic<unsigned long long> configured{0};  // the shared-memory opt-in, once per device (any thread)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -956,7 +966,7 @@ cudaError_t launch_tail(const StepParams& P, const float* S, float* lam, double*
     }
     const int rows = tail_rows(P.nx, P.ny);
     const dim3 g(static_cast<unsigned>((P.nx + kTileX - 1) / kTileX), static_cast<unsigned>((P.ny + rows - 1) / rows));
-    k_rev_tail<W, EXPAND><<<g, kWin, kTailSmem, s>>>(P, S, lam, rows, partials);
+    k_rev_tail<W, EXPAND><<<g, kWin, kTailSmem, s>>>(P, F, S, lam, rows, partials);
     return cudaGetLastError();
 }
 
@@ -1048,7 +1058,9 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = fr[i] + fb[i];
                 const float a = rr * P.inv_rho0_r, b = rb * P.inv_rho0_b;
-                const float inv = 1.0f / (a + b);
+                // the step kernel's arithmetic, bit for bit (its fields replace these
+                // where a replayed step wrote them)
+                const float inv = rcp(__fadd_rn(a, b));
                 const float chr = a * inv, chb = b * inv;
                 const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
                 r4(kHChr, y)[t] = chr;
@@ -1118,8 +1130,9 @@ __global__ void __launch_bounds__(kWin) k_fwd_head(const float* __restrict__ pos
                 const float hk = P.half_sigma * K;
                 const float Gx = fmaf(hk, gx, fmaf(rho, P.gacc_x, P.gvol_x));
                 const float Gy = fmaf(hk, gy, fmaf(rho, P.gacc_y, P.gvol_y));
-                const float ux = fmaf(0.5f, Gx, r4(kHJx, y)[t]) / rho;
-                const float uy = fmaf(0.5f, Gy, r4(kHJy, y)[t]) / rho;
+                const float inv_rho = rcp(rho);
+                const float ux = fmaf(0.5f, Gx, r4(kHJx, y)[t]) * inv_rho;
+                const float uy = fmaf(0.5f, Gy, r4(kHJy, y)[t]) * inv_rho;
                 if (owned(y)) {
                     const size_t o = static_cast<size_t>(y) * nx + xc;
                     S[kGX * n + o] = gx;
@@ -1366,16 +1379,21 @@ void forward_planes(const float* post, const StepParams& P, float* S, cudaStream
 // passes (seven with fixed K).
 template <int O, bool W, bool EXPAND>
 cudaError_t reverse_step(const float* post, const float* lam_post, const StepParams& P, float* S, double* partials,
-                         float* lam_out, cudaStream_t s) {
+                         float* lam_out, cudaStream_t s, const float* fwd) {
     const dim3 g = adj_grid(P);
     if (O == 2 && use_fused(P)) {
-        const cudaError_t e = launch_fwd_head<W>(post, P, S, s);
-        if (e != cudaSuccess) return e;
-        k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
-        return launch_tail<W, EXPAND>(P, S, lam_out, partials, s);
+        // the forward fields of post: written by the replayed step, or recomputed here
+        const float* F = fwd;
+        if (!F) {
+            const cudaError_t e = launch_fwd_head<W>(post, P, S, s);
+            if (e != cudaSuccess) return e;
+            F = S;
+        }
+        k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, F, S, partials);
+        return launch_tail<W, EXPAND>(P, F, S, lam_out, partials, s);
     }
     forward_planes<O, W>(post, P, S, s);
-    k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, partials);
+    k_rev_collide<O, W><<<g, kAT, 0, s>>>(post, lam_post, P, S, S, partials);
     k_rev_force<W><<<g, kAT, 0, s>>>(P, S, partials);
     if (P.curvature_mode == 0) k_rev_normal<W><<<g, kAT, 0, s>>>(P, S);
     k_rev_moments<O, W><<<g, kAT, 0, s>>>(P, S);
@@ -1417,16 +1435,20 @@ cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* sc
     return cudaGetLastError();
 }
 
+bool adj_fused(const StepParams& P) { return P.stencil_order == 2 && use_fused(P); }
+
 int adj_launches_per_step(const StepParams& P) {
-    if (P.stencil_order == 2 && use_fused(P)) return 3;  // fused forward fields, collision pass, fused tail
+    if (adj_fused(P)) return 3;  // fused forward fields, collision pass, fused tail
     return P.curvature_mode == 0 ? 8 : 7;
 }
 
 cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const StepParams& P, float* scratch,
-                                double* partials, float* lam_prev, cudaStream_t s) {
+                                double* partials, float* lam_prev, cudaStream_t s, const float* fwd) {
+    if (fwd && !adj_fused(P)) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     dispatch(P, [&](auto o, auto w) {
-        e = reverse_step<decltype(o)::value, decltype(w)::value, false>(post, lam_post, P, scratch, partials, lam_prev, s);
+        e = reverse_step<decltype(o)::value, decltype(w)::value, false>(post, lam_post, P, scratch, partials, lam_prev,
+                                                                       s, fwd);
     });
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1435,7 +1457,8 @@ cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, co
                                     double* partials, float* lam_pre, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     dispatch(P, [&](auto o, auto w) {
-        e = reverse_step<decltype(o)::value, decltype(w)::value, true>(post, lam_post, P, scratch, partials, lam_pre, s);
+        e = reverse_step<decltype(o)::value, decltype(w)::value, true>(post, lam_post, P, scratch, partials, lam_pre, s,
+                                                                      nullptr);
     });
     return e != cudaSuccess ? e : cudaGetLastError();
 }

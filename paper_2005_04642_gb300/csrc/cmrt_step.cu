@@ -468,12 +468,12 @@ constexpr int min_ctas_per_sm() {
     return Geometry<L>::kBytes + 1024 <= 228 * 1024 / 3 ? 3 : 2;
 }
 // CTA size of a pass: the step is warp-specialised (front + back)
-constexpr int pass_threads(Pass m) { return m == Pass::Step ? kStepThreads : kThreads; }
+constexpr int pass_threads(Pass m) { return m == Pass::Step || m == Pass::StepFields ? kStepThreads : kThreads; }
 // resident CTAs per SM a pass is compiled for: the warp-specialised step
 // keeps two CTAs (16 warps) per SM in every storage form
 template <class L>
 constexpr int pass_ctas_per_sm(Pass m) {
-    return m == Pass::Step ? 2 : min_ctas_per_sm<L>();
+    return m == Pass::Step || m == Pass::StepFields ? 2 : min_ctas_per_sm<L>();
 }
 
 // Diagnostics accumulators of one thread (Pass::Diag).
@@ -504,7 +504,8 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                                            char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
                                            const int rows, const FieldOut& fo, unsigned* __restrict__ flag,
                                            DiagAcc& acc) {
-    constexpr bool kWS = MODE == Pass::Step;
+    constexpr bool kStep = MODE == Pass::Step || MODE == Pass::StepFields;
+    constexpr bool kWS = kStep;
     const bool front = !kWS || threadIdx.x < kThreads;  // warp-uniform
     const int t = front ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) - kThreads;
     const int nx = P.nx, ny = P.ny;
@@ -514,6 +515,13 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
     const int s_last = y_end + 3;
     const int iters = (y_end - y0) + 8;
     auto row_ok = [&](int r) { return !WALLS || (r >= 0 && r < ny); };
+    // Pass::StepFields: the forward fields of the nodes this tile owns go to fo.fwd
+    const int gx_own = x0 + t - kHalo;
+    const bool own_col = t >= kHalo && t < kWin - kHalo && gx_own < nx;
+    auto owned = [&](int r) { return MODE == Pass::StepFields && own_col && r >= y0 && r < y_end; };
+    auto fwd = [&](int plane, int r) -> float& {
+        return fo.fwd[static_cast<size_t>(plane) * nodes + static_cast<size_t>(r) * nx + gx_own];
+    };
 
     typename L::template Plan<VEC> plan;
     plan.init(x0, nx, nodes);
@@ -543,7 +551,7 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             // colour fractions: rho^N = 2 chi_R - 1 = 1 - 2 chi_B (Eq. equ_rhoN_def);
             // the smaller of the two keeps the digits that rho^N, stored in FP32
             // next to -1 or +1, would lose
-            const float inv_ab = rcp(a + b);
+            const float inv_ab = rcp(__fadd_rn(a, b));  // not contracted: the adjoint recomputes it
             const float chr = a * inv_ab;
             const float chb = b * inv_ab;
             const float phip = fmaf(P.phip_r, rr, P.phip_b * rb);  // App. A, Phi'
@@ -553,6 +561,13 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             R.rho(ya)[t] = rr + rb;
             R.jx(ya)[t] = jx;
             R.jy(ya)[t] = jy;
+            if (owned(ya)) {
+                fwd(kFwdRR, ya) = rr;
+                fwd(kFwdRB, ya) = rb;
+                fwd(kFwdCHR, ya) = chr;
+                fwd(kFwdCHB, ya) = chb;
+                fwd(kFwdPHIP, ya) = phip;
+            }
             if (WALLS && ya == 0) {  // even mirror beyond y = -1/2
                 R.chiR(-1)[t] = chr;
                 R.chiB(-1)[t] = chb;
@@ -587,6 +602,10 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             R.grad(yb, 1)[t] = gy;
             R.nh(yb, 0)[t] = nhx;
             R.nh(yb, 1)[t] = nhy;
+            if (owned(yb)) {
+                fwd(kFwdGX, yb) = gx;
+                fwd(kFwdGY, yb) = gy;
+            }
             if (WALLS && yb == 0) {  // reflected normal beyond the wall
                 R.nh(-1, 0)[t] = nhx;
                 R.nh(-1, 1)[t] = -nhy;
@@ -625,6 +644,13 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             R.G(yc, 1)[t] = Gy;
             R.u(yc, 0)[t] = ux;
             R.u(yc, 1)[t] = uy;
+            if (owned(yc)) {
+                fwd(kFwdK, yc) = K;
+                fwd(kFwdGFX, yc) = Gx;
+                fwd(kFwdGFY, yc) = Gy;
+                fwd(kFwdUX, yc) = ux;
+                fwd(kFwdUY, yc) = uy;
+            }
             if (WALLS && yc == 0) {  // no-slip: odd mirror of u
                 R.u(-1, 0)[t] = -ux;
                 R.u(-1, 1)[t] = -uy;
@@ -652,7 +678,7 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             const float rho = rr + rb;
             const float ux = R.u(yd, 0)[t];
             const float uy = R.u(yd, 1)[t];
-            if (MODE == Pass::Step) {
+            if (kStep) {
                 if (!isfinite(rho)) atomicOr(flag, 1u);
                 const float Gx = R.G(yd, 0)[t];
                 const float Gy = R.G(yd, 1)[t];
@@ -1001,6 +1027,13 @@ int chain_rows(int nx, int ny, int sms, int precision) {
 
 cudaError_t launch_step(const void* src, void* dst, const StepParams& P, int rows, unsigned* flag, cudaStream_t s) {
     return launch_chain<Pass::Step>(src, dst, P, rows, FieldOut{}, flag, nullptr, s);
+}
+
+cudaError_t launch_step_fields(const float* src, float* dst, const StepParams& P, int rows, unsigned* flag,
+                               float* fwd, cudaStream_t s) {
+    FieldOut fo{};
+    fo.fwd = fwd;
+    return launch_layout<LayoutF32, Pass::StepFields>(src, dst, P, rows, fo, flag, nullptr, s);
 }
 
 cudaError_t launch_fields(const void* src, const StepParams& P, int rows, FieldOut out, cudaStream_t s) {

@@ -192,19 +192,31 @@ def test_fused_kernels_equal_plane_passes(wall):
     assert np.abs(r1 - r2).max() <= 1e-5 * np.abs(r2).max()
 
 
-def test_checkpoint_interval_gives_identical_gradients():
+@pytest.mark.parametrize("fused,wall", [(2, False), (1, False), (1, True)], ids=["planes", "fused", "fused_walls"])
+def test_checkpoint_interval_gives_identical_gradients(fused, wall):
+    """Every checkpoint interval gives the same objective and gradients, bit
+    for bit.  With the fused reverse step, K = 1 recomputes every state's
+    forward fields in the reverse step, while K > 1 takes them from the
+    replayed steps that wrote them (all but a segment's last state): the two
+    sources must agree exactly."""
     nsteps = 12
-    d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4)
+    d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4, wall=wall)
+    d["adjoint_fused"] = fused
     outs = []
+    launches = {}
     for K in (1, 5, 12, 200):
         lat = cm.Lattice(d, rn0.astype(np.float32), None)
         J, g, grn = lat.adjoint(nsteps, target.astype(np.float32), ckpt_every=K, want_rho_n0=True)
         outs.append((J, g, grn.cpu().numpy()))
+        launches[K] = lat.launches
         lat.close()
     for J, g, grn in outs[1:]:
         assert J == outs[0][0]
         assert g == outs[0][1]
         assert np.array_equal(grn, outs[0][2])
+    # one segment of 12 replays 11 steps; where they write the forward fields,
+    # 11 reverse steps skip their recomputation (one launch each)
+    assert launches[12] - launches[1] == (0 if fused == 1 else 11)
 
 
 def test_recorded_segment_graphs_are_replayed_exactly():
