@@ -478,7 +478,7 @@ def run_variants(args, cm, I, stream, fp32_ms):
     d, rn, u = make_workload(args.side)
     cells = d["nx"] * d["ny"]
     steps = max(20, args.steps // 4)
-    for name, prec, nbytes in (("fp16", 2, 88), ("bf16", 1, 88)):
+    for name, prec, nbytes in (("fp16", 2, 128), ("bf16", 1, 128)):
         ms, _ = time_steps(cm, dict(d, precision=prec), rn, u, steps, 5, stream)
         out[f"{name}_{WORKLOAD if args.side == N_SIDE else args.side}"] = {
             "value": cells / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "speedup_vs_fp32": fp32_ms / ms,
@@ -488,7 +488,7 @@ def run_variants(args, cm, I, stream, fp32_ms):
         d, rn, u = I.buoyant_drops()
         cells = d["nx"] * d["ny"]
         base = None
-        for name, prec, nbytes in (("fp32", 0, 144), ("fp16", 2, 88), ("bf16", 1, 88)):
+        for name, prec, nbytes in (("fp32", 0, 144), ("fp16", 2, 128), ("bf16", 1, 128)):
             ms, diag = time_steps(cm, dict(d, precision=prec), rn, u, steps, 5, stream)
             base = base or ms
             out[f"{name}_buoyant_16384x8192_walls_256drops"] = {
@@ -684,7 +684,7 @@ def run_profile_step(args):
     stream = torch.cuda.current_stream()
     ms, diag = time_steps(cm, d, rn, u, args.steps, args.warmup, stream)
     cells = d["nx"] * d["ny"]
-    nbytes = 144 if args.precision == 0 else 88
+    nbytes = 144 if args.precision == 0 else 128
     print(json.dumps({"side": args.side, "precision": args.precision, "ms_per_step": ms,
                       "MLUPS": cells / (ms * 1e-3) / 1e6, "GBs": nbytes * cells / (ms * 1e-3) / 1e9,
                       "nonfinite": diag["nonfinite"]}), flush=True)

@@ -56,8 +56,9 @@ extern "C" {
  * meaning; bindings check it (cmrt_abi_version) before use.  6: per-context
  * step graphs (cmrt_set_graph_steps, cmrt_get_graph_steps).  7: checkpoint
  * and restart (cmrt_save_bytes, cmrt_save, cmrt_load).  8: precision_reference
- * 0 is the node-mixture reference, the pure-colour one moved to 2. */
-#define CMRT_ABI_VERSION 8
+ * 0 is the node-mixture reference, the pure-colour one moved to 2.  9: the
+ * 16-bit record carries reference dipoles and the rest populations (64 B/node). */
+#define CMRT_ABI_VERSION 9
 
 typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
 typedef struct cmrt_batch cmrt_batch; /* opaque, owned by the library */
@@ -100,9 +101,13 @@ typedef struct {
     double fixed_K;
     int32_t ghost_N_mode;    /* 0: N relaxes to h^(6).f^(0) (App. A); 1: N relaxes to 0 (Table 1) */
     int32_t precision;       /* population storage in HBM: 0 = FP32 (72 B/node); 1 = BF16, 2 = FP16
-                                (44 B/node: rho_R, rho_B in FP32 plus nine 16-bit pairs of
-                                deviations C_i - rho_C psi_i, FP16 ones times 2^k with k = 14 for
-                                bulk densities up to 1); arithmetic is FP32 in all cases           */
+                                (64 B/node: rho_R, rho_B and the rest populations R_0, B_0 in
+                                FP32; four 16-bit (red, blue) pairs of reference dipoles -- the
+                                equilibrium's velocity term and the recolour's segregation term
+                                (Eq. eq_re_color) per link direction; eight 16-bit pairs of
+                                deviations C_i - rho_C psi_i -/+ D_C of the moving links, FP16
+                                ones times 2^k with k = 14 for bulk densities up to 1);
+                                arithmetic is FP32 in all cases                                   */
     int32_t diag_every;      /* cmrt_step checks the non-finite flag every diag_every steps
                                 (synchronising the stream then); 0 = only at cmrt_diagnostics    */
     int32_t precision_reference; /* 16-bit storage reference psi_i: 0 = phi_i of Eq. eq_phi at the

@@ -255,14 +255,12 @@ StepParams derive(const cmrt_params& p) {
     s.fixed_K = static_cast<float>(p.fixed_K);
     s.precision = p.precision;
     s.precision_reference = p.precision_reference;
-    // 16-bit storage keeps C_i - rho_C psi_i.  Reference 0: phi_i of Eq. eq_phi
-    // at the node's own mixture (computed in the kernels from the stored
-    // densities with psi_axis = mix_r rho_R + mix_b rho_B over rho);
-    // reference 1: the lattice weights w_i; reference 2: phi_i of the pure
-    // colour C (alpha_C).  The constant FP32 weights are adjusted so that
-    // psi_0 + 4 psi_axis + 4 psi_diag is exactly 1 in real arithmetic: any
-    // reference decodes correctly, but one whose weights do not sum to 1 would
-    // bias colour mass every step.
+    // 16-bit storage keeps C_i - rho_C psi_i -/+ D_C for the moving links.
+    // Reference 0: phi_i of Eq. eq_phi at the node's own mixture (computed in
+    // the kernels from the stored densities with psi_axis = mix_r rho_R +
+    // mix_b rho_B over rho); reference 1: the lattice weights w_i; reference
+    // 2: phi_i of the pure colour C (alpha_C).  Every reference has psi_axis a
+    // multiple of 2^-24 and psi_diag = psi_axis / 4, both exact in FP32.
     s.mix_r = static_cast<float>((1.0 - p.alpha_r) / 5.0);
     s.mix_b = static_cast<float>((1.0 - p.alpha_b) / 5.0);
     // FP16 deviations are stored scaled by 2^k so that small ones stay in
@@ -280,15 +278,12 @@ StepParams derive(const cmrt_params& p) {
     }
     s.dev_scale = static_cast<float>(std::ldexp(1.0, k));
     s.dev_unscale = static_cast<float>(std::ldexp(1.0, -k));
-    const double wts[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
     auto weights = [&](double alpha, float out[3]) {
-        const double axis = p.precision_reference == 1 ? wts[1] : 1.8 * (1.0 - alpha) * wts[1];
-        const double diag = p.precision_reference == 1 ? wts[2] : 1.8 * (1.0 - alpha) * wts[2];
-        const double fa = static_cast<float>(axis);
-        const double moving = std::ldexp(std::nearbyint(std::ldexp(4.0 * fa + 4.0 * static_cast<float>(diag), 24)), -24);
-        out[1] = static_cast<float>(fa);
-        out[2] = static_cast<float>((moving - 4.0 * fa) / 4.0);   // exact: a multiple of 2^-30
-        out[0] = static_cast<float>(1.0 - moving);                // exact: a multiple of 2^-24
+        const double axis = p.precision_reference == 1 ? 1.0 / 9.0 : (1.0 - alpha) / 5.0;
+        const double pa = std::ldexp(std::nearbyint(std::ldexp(axis, 24)), -24);  // a multiple of 2^-24
+        out[1] = static_cast<float>(pa);
+        out[2] = static_cast<float>(pa / 4.0);        // exact
+        out[0] = static_cast<float>(1.0 - 5.0 * pa);  // the rest link's share (the record stores it directly)
     };
     weights(p.alpha_r, s.psi_r);
     weights(p.alpha_b, s.psi_b);

@@ -147,27 +147,27 @@ __global__ void k_unstream_in(const float* __restrict__ pre, int nx, int ny, int
     }
 }
 
-// 16-bit storage (see cmrt_step.cu): a node keeps (rho'_R, rho'_B) in FP32 and,
-// per link, the deviations d_C,i = C_i - rho_C psi_i as a 16-bit pair, with
-// rho_C the sum of the record's own nine populations of colour C and
-// rho'_C = rho_C - sum_i round(d_C,i), so that decoding conserves rho_C.
-// The reference weights (rest, axis, diagonal) as (red, blue) pairs: the
-// node's mixture (precision_reference 0; the same exact-sum rounding as the
-// step kernel's) or per-colour constants.
-__device__ __forceinline__ void ref_weights(float rr, float rb, const StepParams& P, float2 (&w)[3]) {
+// 16-bit storage (see cmrt_step.cu): a node keeps (rho_R, rho_B) and the
+// rest populations (R_0, B_0) in FP32 and twelve 16-bit (red, blue) pairs:
+// four reference dipoles D_j and the deviations d_C,i of links 1..8, decoded
+// as C_i = rho_C psi_i +/- D_C,dip(i) + d_C,i / 2^k.  Here the dipoles are
+// those of the record's own populations: their velocity j / rho and their
+// segregation vector S, the antisymmetric part of the colour split C_i -
+// (rho_C / rho) f_i along x and y (a state the step wrote gets its own S
+// back; any other state a valid one, whose rest the deviations carry).  The
+// rest populations are the remainder of rho_C after the moving links as the
+// step kernel decodes them, so that decoding conserves rho_C.  The axis reference weight (diagonal = axis
+// / 4) as a (red, blue) pair: the node's mixture (precision_reference 0; the
+// same rounding as the step kernel's) or per-colour constants.
+__device__ __forceinline__ float2 ref_weight_a(float rr, float rb, const StepParams& P) {
     if (P.precision_reference == 0) {
         float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * __fdividef(1.0f, rr + rb);
         s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
         const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);
-        const float p0 = fmaf(-4.0f, pa, 1.0f - pa);
-        w[0] = make_float2(p0, p0);
-        w[1] = make_float2(pa, pa);
-        w[2] = make_float2(0.25f * pa, 0.25f * pa);
-    } else {
-        for (int k = 0; k < 3; ++k) w[k] = make_float2(P.psi_r[k], P.psi_b[k]);
+        return make_float2(pa, pa);
     }
+    return make_float2(P.psi_r[1], P.psi_b[1]);
 }
-__device__ __forceinline__ int ref_class(int i) { return i == 0 ? 0 : ((i & 1) ? 2 : 1); }
 __device__ __forceinline__ unsigned pack2(float a, float b, int precision) {
     if (precision == kPrecF16) {
         const __half2 h = __floats2half2_rn(a, b);
@@ -185,29 +185,64 @@ __global__ void k_encode(const float* __restrict__ post, StepParams P, char* __r
     const size_t nodes = static_cast<size_t>(P.nx) * P.ny;
     for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < nodes;
          n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        float r[9], b[9], rr = 0.f, rb = 0.f;
+        float r[9], b[9], rr = 0.f, rb = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             r[i] = post[i * nodes + n];
             b[i] = post[(9 + i) * nodes + n];
             rr += r[i];
             rb += b[i];
+            jx += lcx(i) * (r[i] + b[i]);
+            jy += lcy(i) * (r[i] + b[i]);
         }
-        unsigned* dev = reinterpret_cast<unsigned*>(state + nodes * 8);
-        float2 w[3];
-        ref_weights(rr, rb, P, w);
-        float er = 0.f, eb = 0.f;  // rounded deviations, absorbed by the stored densities
+        const float rho = rr + rb;
+        // S from the antisymmetric part of the red split a_i = R_i - (rho_R / rho) f_i:
+        // a_8 - a_4 = 2 w_axis S_x, a_2 - a_6 = 2 w_axis S_y
+        const float kr = rr / rho;
+        const float a8 = fmaf(-kr, r[8] + b[8], r[8]), a4 = fmaf(-kr, r[4] + b[4], r[4]);
+        const float a2 = fmaf(-kr, r[2] + b[2], r[2]), a6 = fmaf(-kr, r[6] + b[6], r[6]);
+        unsigned* pairs = reinterpret_cast<unsigned*>(state + nodes * 16);
+        float2 D[4];
+        dipoles16(rr, rb, jx / rho, jy / rho, (a8 - a4) * (0.5f / lw(8)), (a2 - a6) * (0.5f / lw(2)), D);
+        for (int j = 0; j < 4; ++j) {
+            const unsigned h = pack2(D[j].x, D[j].y, P.precision);
+            pairs[j * nodes + n] = h;
+            D[j] = unpack2(h, P.precision);  // the dipole as stored
+        }
+        const float2 wa = ref_weight_a(rr, rb, P);
+        const float2 refa = make_float2(__fmul_rn(rr, wa.x), __fmul_rn(rb, wa.y));  // the decoder's
         const float S = P.dev_scale;  // a power of two: the scaled deviation is the deviation, scaled exactly
+        float sr = 0.f, sb = 0.f;     // the moving links as decoded, for the rest populations
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float2 wi = w[ref_class(i)];
-            const unsigned h = pack2(fmaf(-rr * S, wi.x, r[i] * S), fmaf(-rb * S, wi.y, b[i] * S), P.precision);
-            const float2 back = unpack2(h, P.precision);
-            er = fmaf(back.x, P.dev_unscale, er);
-            eb = fmaf(back.y, P.dev_unscale, eb);
-            dev[i * nodes + n] = h;
+        for (int i = 1; i < 9; ++i) {
+            const float wr = (i & 1) ? 0.25f * wa.x : wa.x, wb = (i & 1) ? 0.25f * wa.y : wa.y;
+            const float2 Dj = D[dip_index(i)];
+            const float sg = dip_neg(i) ? -1.0f : 1.0f;
+            const float cr = r[i] - sg * Dj.x, cb = b[i] - sg * Dj.y;
+            const unsigned h = pack2(fmaf(-rr * S, wr, cr * S), fmaf(-rb * S, wb, cb * S), P.precision);
+            pairs[(3 + i) * nodes + n] = h;
+            const float2 dd = unpack2(h, P.precision);
+            float xr, xb;
+            if (i & 1) {
+                xr = __fmaf_rn(refa.x, 0.25f, __fmul_rn(dd.x, P.dev_unscale));
+                xb = __fmaf_rn(refa.y, 0.25f, __fmul_rn(dd.y, P.dev_unscale));
+            } else {
+                xr = __fmaf_rn(dd.x, P.dev_unscale, refa.x);
+                xb = __fmaf_rn(dd.y, P.dev_unscale, refa.y);
+            }
+            if (dip_neg(i)) {
+                xr = __fmaf_rn(Dj.x, -1.0f, xr);
+                xb = __fmaf_rn(Dj.y, -1.0f, xb);
+            } else {
+                xr = __fadd_rn(xr, Dj.x);
+                xb = __fadd_rn(xb, Dj.y);
+            }
+            sr = __fadd_rn(sr, xr);
+            sb = __fadd_rn(sb, xb);
         }
-        reinterpret_cast<float2*>(state)[n] = make_float2(rr - er, rb - eb);
+        float2* own = reinterpret_cast<float2*>(state) + n;
+        own[0] = make_float2(rr, rb);
+        own[nodes] = make_float2(__fsub_rn(rr, sr), __fsub_rn(rb, sb));
     }
 }
 
@@ -215,18 +250,36 @@ __global__ void k_decode(const char* __restrict__ state, StepParams P, float* __
     const size_t nodes = static_cast<size_t>(P.nx) * P.ny;
     for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < nodes;
          n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const float2 rho = reinterpret_cast<const float2*>(state)[n];
-        const unsigned* dev = reinterpret_cast<const unsigned*>(state + nodes * 8);
-        float2 w[3];
-        ref_weights(rho.x, rho.y, P, w);
-        // the step kernel's decode: reference pair rho' psi rounded once, plus the deviation
-        float2 ref[3];
-        for (int k = 0; k < 3; ++k) ref[k] = make_float2(__fmul_rn(rho.x, w[k].x), __fmul_rn(rho.y, w[k].y));
+        const float2* own = reinterpret_cast<const float2*>(state) + n;
+        const float2 rho = own[0], rest = own[nodes];
+        const unsigned* pairs = reinterpret_cast<const unsigned*>(state + nodes * 16);
+        // the step kernel's decode: the axis reference pair rho psi_a (diagonal:
+        // over 4) plus the deviation, rounded once; then the dipole
+        const float2 wa = ref_weight_a(rho.x, rho.y, P);
+        const float2 refa = make_float2(__fmul_rn(rho.x, wa.x), __fmul_rn(rho.y, wa.y));
+        post[n] = rest.x;
+        post[9 * nodes + n] = rest.y;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float2 d = unpack2(dev[i * nodes + n], P.precision);
-            post[i * nodes + n] = __fmaf_rn(d.x, P.dev_unscale, ref[ref_class(i)].x);
-            post[(9 + i) * nodes + n] = __fmaf_rn(d.y, P.dev_unscale, ref[ref_class(i)].y);
+        for (int i = 1; i < 9; ++i) {
+            const float2 d = unpack2(pairs[(3 + i) * nodes + n], P.precision);
+            float cr, cb;
+            if (i & 1) {
+                cr = __fmaf_rn(refa.x, 0.25f, __fmul_rn(d.x, P.dev_unscale));
+                cb = __fmaf_rn(refa.y, 0.25f, __fmul_rn(d.y, P.dev_unscale));
+            } else {
+                cr = __fmaf_rn(d.x, P.dev_unscale, refa.x);
+                cb = __fmaf_rn(d.y, P.dev_unscale, refa.y);
+            }
+            const float2 D = unpack2(pairs[dip_index(i) * nodes + n], P.precision);
+            if (dip_neg(i)) {
+                cr = __fmaf_rn(D.x, -1.0f, cr);
+                cb = __fmaf_rn(D.y, -1.0f, cb);
+            } else {
+                cr = __fadd_rn(cr, D.x);
+                cb = __fadd_rn(cb, D.y);
+            }
+            post[i * nodes + n] = cr;
+            post[(9 + i) * nodes + n] = cb;
         }
     }
 }

@@ -102,6 +102,27 @@ __device__ __forceinline__ void segregation(float sx, float sy, float (&seg)[9])
     seg[7] = -d3;
 }
 
+// Reference dipoles of the 16-bit storage (cmrt_step.cu): per (red, blue)
+// pair, the velocity term of the equilibrium, 3 w_i rho_C c_i . u, plus the
+// segregation term of the recolour (Eq. eq_re_color), +/- w_i S . c-hat_i
+// (red +, blue -), for the links c = (1, 0) (D[0]), (0, 1) (D[1]), (1, 1)
+// (D[2]) and (-1, 1) (D[3]); the opposite links carry the negatives.
+__device__ __forceinline__ void dipoles16(float rr, float rb, float ux, float uy, float sx, float sy,
+                                          float2 (&D)[4]) {
+    const float ar = 3.0f * rr, ab = 3.0f * rb;
+    D[0] = make_float2(lw(8) * fmaf(ar, ux, sx), lw(8) * fmaf(ab, ux, -sx));
+    D[1] = make_float2(lw(2) * fmaf(ar, uy, sy), lw(2) * fmaf(ab, uy, -sy));
+    const float up = ux + uy, um = uy - ux;
+    const float sp = chx(1) * (sx + sy), sm = chx(1) * (sy - sx);
+    D[2] = make_float2(lw(1) * fmaf(ar, up, sp), lw(1) * fmaf(ab, up, -sp));
+    D[3] = make_float2(lw(1) * fmaf(ar, um, sm), lw(1) * fmaf(ab, um, -sm));
+}
+// which dipole link i >= 1 carries, and whether negated (links 4, 6, 5, 7)
+__host__ __device__ constexpr int dip_index(int i) {
+    return (i == 8 || i == 4) ? 0 : (i == 2 || i == 6) ? 1 : (i == 1 || i == 5) ? 2 : 3;
+}
+__host__ __device__ constexpr bool dip_neg(int i) { return i == 4 || i == 6 || i == 5 || i == 7; }
+
 // Collision in moment space of one node in increment form (App. A, Eq. 38
 // minus m, and the reconstruction of Eq. eq84): f+ = f + M^{-1} dm with
 // dm = Lambda (m^(0) - m) + S.  Inputs: the pre-collision populations f, the

@@ -102,7 +102,7 @@ enum class Pass : int { Step = 0, Fields = 1, Diag = 2, StepFields = 3 };
 // Number of FP64 partial sums each CTA of the diagnostics pass writes.
 constexpr int kDiagSlots = 6;  // mass_r, mass_b, mom_x, mom_y, max|u|^2, non-finite count
 
-// Bytes of one node of the state for a storage precision (72 FP32, 44 16-bit).
+// Bytes of one node of the state for a storage precision (72 FP32, 64 16-bit).
 size_t state_node_bytes(int precision);
 // grid of the chain kernel for a lattice, with `rows` rows per CTA
 dim3 chain_grid(int nx, int ny, int rows);

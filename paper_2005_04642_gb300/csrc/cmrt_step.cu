@@ -4,16 +4,19 @@
 // Data layout in HBM: the state is the post-collision (pre-streaming)
 // populations P_{t-1}.  With FP32 storage they are 18 planes
 // float[18][ny][nx] (red links 0..8, then blue links 0..8).  With 16-bit
-// storage (FP16 or BF16) a node keeps its two colour densities in FP32 and
-// nine 16-bit pairs of deviations d_{C,i} = C_i - rho_C psi^C_i from a
-// reference that scales with the node's own colour density: plane 0 is
-// float2[ny][nx] (rho'_R, rho'_B), planes 1..9 are 16-bit pairs (d_R,i, d_B,i).
-// The stored densities rho'_C = rho_C - sum_i round(d_C,i) absorb the
-// rounding, so a record decodes to populations summing to rho_C.
+// storage (FP16 or BF16) a node keeps its two colour densities and its two
+// rest populations in FP32 and twelve 16-bit (red, blue) pairs: four
+// reference dipoles -- the equilibrium's velocity term and the recolour's
+// segregation term -- and the deviations d_{C,i} = C_i - rho_C psi_i -/+ D_C
+// of the eight moving links from a reference that scales with the node's own
+// colour density: planes 0 and 1 are float2[ny][nx] (rho_R, rho_B) and
+// (R_0, B_0), planes 2..13 16-bit pairs.  The rest populations are the
+// remainder of the densities after the decoded moving links, so a record
+// decodes to populations summing to rho_C.
 // One launch gathers the pre-collision populations f(t) = stream(P_{t-1})
 // on the fly ("pull"), performs the whole per-node update and writes P_t to
 // the other buffer at the node itself, so every HBM access is coalesced:
-// 72 B (FP32) or 44 B (16-bit) read and as much written per node.
+// 72 B (FP32) or 64 B (16-bit) read and as much written per node.
 //
 // A CTA owns a strip of 120 columns (plus 4 halo columns on each side, 128
 // in all: one thread per column in each of its thread groups) and marches
@@ -194,76 +197,98 @@ struct LayoutF32 {
     // R++ + B++ = f+ holds to one rounding of the majority.  (sx, sy) is the
     // red segregation vector beta phi rho_R rho_B / rho e of Eq. eq_re_color.
     __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
-                                                 float rr, float rb, float inv_rho, float sx, float sy,
-                                                 const StepParams&) {
+                                                 float rr, float rb, float inv_rho, float sx, float sy, float,
+                                                 float, const StepParams&) {
         store_recoloured_f32(reinterpret_cast<float*>(dst) + node, nodes, fp, rr, rb, inv_rho, sx, sy);
     }
 };
 
-// 16-bit deviations (H = __half2 or __nv_bfloat162) from rho_C psi_i.
+// 16-bit deviations (H = __half2 or __nv_bfloat162).
 //
-// A ring row keeps, per window column, the stored densities (rho'_R, rho'_B)
-// as copied, the reference pairs (rho'_R psi^R_k, rho'_B psi^B_k) of the three
-// link classes k (rest, axis, diagonal), and the nine 16-bit deviation pairs
-// as copied.  The reference pairs are filled once per row, by the thread that
-// copied the column's densities, as soon as its copy has landed (prep); a
-// gathered population is then one packed add, reference + deviation.
+// Record of a node: two float2 planes -- the colour densities (rho_R,
+// rho_B) and the rest populations (R_0, B_0) -- then twelve planes of 16-bit
+// (red, blue) pairs -- four reference dipoles D_0..D_3, then the deviations
+// d_i of the moving links i = 1..8 -- decoded as
+//   C_i = rho_C psi_i + (+/-) D_C,dip(i) + d_C,i / 2^k      (i >= 1)
+// (dip_index, dip_neg).  psi_i are the reference weights (axis psi_a,
+// diagonal psi_a / 4).  The step stores as dipoles (dipoles16) the
+// equilibrium's velocity term, with the node's post-collision velocity, and
+// the recolour's segregation term (Eq. eq_re_color), so that its deviations
+// are only the non-equilibrium and second-order parts of the populations:
+// tens of times smaller than their deviations from rho_C psi_i, and so is
+// their 16-bit rounding.  The dipoles are reference values, stored rounded
+// and used as stored: their rounding only moves a little into the
+// deviations.  The rest populations are the remainder of rho_C after the
+// decoded moving links, so that a record decodes to populations summing to
+// rho_C.  Any pair of population sets is representable.
+//
+// A ring row keeps, per window column, the densities as copied --
+// overwritten by the thread that copied them, as soon as its copy has landed
+// (prep), with the axis reference pair (rho_R psi^R_a, rho_B psi^B_a) (the
+// diagonal one is it over 4, exactly) -- and the rest populations and the
+// twelve 16-bit pairs as copied.
 template <class H>
 struct Layout16 {
-    static constexpr int kRhoBytes = kWin * 8;      // float2 (rho'_R, rho'_B) per column
-    static constexpr int kRefBytes = 3 * kWin * 8;  // float2 reference pair per class and column
-    static constexpr int kDevBytes = kWin * 4;      // one 16-bit pair per column and link
-    static constexpr int kDevOff = kRhoBytes + kRefBytes;
-    static constexpr int kSlotBytes = kDevOff + 9 * kDevBytes;
-    static constexpr int kDevChunks = 9 * kDevBytes / 16;
-    static constexpr int kVecIters = (kDevChunks + kThreads - 1) / kThreads;
+    static constexpr int kRefBytes = kWin * 8;    // float2 per column: (rho_R, rho_B) -> axis reference pair
+    static constexpr int kRestBytes = kWin * 8;   // float2 per column: (R_0, B_0)
+    static constexpr int kPairBytes = kWin * 4;   // one 16-bit pair per column and plane
+    static constexpr int kPairOff = kRefBytes + kRestBytes;
+    static constexpr int kPairPlanes = 12;        // four dipoles, eight deviations
+    static constexpr int kSlotBytes = kPairOff + kPairPlanes * kPairBytes;
+    static constexpr int kPairChunks = kPairPlanes * kPairBytes / 16;
+    static constexpr int kVecIters = (kPairChunks + kThreads - 1) / kThreads;
     static constexpr bool kPrep = true;
-    static constexpr size_t node_bytes() { return 8 + 9 * 4; }
+    static constexpr size_t node_bytes() { return 16 + kPairPlanes * 4; }
 
     __device__ __forceinline__ static float2 to2(H v);
     __device__ __forceinline__ static H from2(float a, float b);
     __device__ __forceinline__ static H from2x(float2 v) { return from2(v.x, v.y); }
 
-    // Each thread copies the densities of its own window column (8 bytes) and
-    // a share of the deviation planes (16-byte chunks of four columns, or its
-    // own column's four bytes per plane when nx is not a multiple of 4).
+    // Each thread copies the densities and rest populations of its own window
+    // column (8 bytes each) and a share of the pair planes (16-byte chunks of
+    // four columns, or its own column's four bytes per plane when nx is not a
+    // multiple of 4).
     template <bool VEC>
     struct Plan {
-        static constexpr int kN = VEC ? kVecIters : 9;
+        static constexpr int kN = VEC ? kVecIters : kPairPlanes;
         unsigned soff[kN];
         size_t goff[kN];  // byte offset of the chunk in row 0 of its plane
-        unsigned rho_soff;
-        size_t rho_goff;
+        unsigned own_soff;
+        size_t own_goff;  // byte offset of the column in row 0 of the densities' plane
+        size_t rest_off;  // bytes from the densities' plane to the rest populations'
         int n;
         __device__ __forceinline__ void init(int x0, int nx, size_t nodes) {
             const int gx = wrap(x0 - kHalo + static_cast<int>(threadIdx.x), nx);
-            rho_soff = threadIdx.x * 8;
-            rho_goff = static_cast<size_t>(gx) * 8;
+            own_soff = threadIdx.x * 8;
+            own_goff = static_cast<size_t>(gx) * 8;
+            rest_off = nodes * 8;
             n = 0;
             if (VEC) {
-                constexpr int kPer = kDevBytes / 16;  // chunks per plane row
+                constexpr int kPer = kPairBytes / 16;  // chunks per plane row
 #pragma unroll
                 for (int m = 0; m < kN; ++m) {
                     const int c = threadIdx.x + m * kThreads;
                     const int p = c / kPer;
                     const int w4 = (c - p * kPer) * 4;
-                    soff[m] = static_cast<unsigned>(kDevOff + p * kDevBytes + w4 * 4);
-                    goff[m] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 +
+                    soff[m] = static_cast<unsigned>(kPairOff + p * kPairBytes + w4 * 4);
+                    goff[m] = nodes * 16 + static_cast<size_t>(p) * nodes * 4 +
                               static_cast<size_t>(wrap(x0 - kHalo + w4, nx)) * 4;
-                    if (c < kDevChunks) n = m + 1;
+                    if (c < kPairChunks) n = m + 1;
                 }
             } else {
 #pragma unroll
-                for (int p = 0; p < 9; ++p) {
-                    soff[p] = static_cast<unsigned>(kDevOff + p * kDevBytes + threadIdx.x * 4);
-                    goff[p] = nodes * 8 + static_cast<size_t>(p) * nodes * 4 + static_cast<size_t>(gx) * 4;
+                for (int p = 0; p < kPairPlanes; ++p) {
+                    soff[p] = static_cast<unsigned>(kPairOff + p * kPairBytes + threadIdx.x * 4);
+                    goff[p] = nodes * 16 + static_cast<size_t>(p) * nodes * 4 + static_cast<size_t>(gx) * 4;
                 }
                 n = kN;
             }
         }
         __device__ __forceinline__ void issue(unsigned slot_addr, const char* state, int gy, int nx) const {
             const size_t row_nodes = static_cast<size_t>(gy) * nx;
-            cp_async8(slot_addr + rho_soff, state + rho_goff + row_nodes * 8);
+            const char* own = state + own_goff + row_nodes * 8;
+            cp_async8(slot_addr + own_soff, own);
+            cp_async8(slot_addr + kRefBytes + own_soff, own + rest_off);
 #pragma unroll
             for (int m = 0; m < kN; ++m) {
                 if (m < n) {
@@ -275,83 +300,103 @@ struct Layout16 {
         }
     };
 
-    // Reference weights (psi_rest, psi_axis, psi_diag) of a node, as (red, blue)
-    // pairs.  precision_reference 0: phi_i of Eq. eq_phi at the node's own
-    // mixture, psi_axis = ((1 - alpha_R) rho_R + (1 - alpha_B) rho_B) / (5 rho)
-    // rounded to a multiple of 2^-24, psi_diag = psi_axis / 4 and psi_rest =
-    // 1 - 5 psi_axis: all three exact in FP32, so psi_rest + 4 psi_axis + 4
-    // psi_diag = 1 exactly and decoding conserves each colour's mass.  Other
+    // Axis reference weight psi_a of a node as a (red, blue) pair; psi_diag =
+    // psi_a / 4.  precision_reference 0: phi_i of Eq. eq_phi at the node's own
+    // mixture, psi_a = ((1 - alpha_R) rho_R + (1 - alpha_B) rho_B) / (5 rho)
+    // rounded to a multiple of 2^-24 (exact in FP32, as is psi_a / 4).  Other
     // references: per-colour constants (psi_r, psi_b).
-    __device__ __forceinline__ static void weights(float rr, float rb, float inv_rho, const StepParams& P,
-                                                   float2& w0, float2& wa, float2& wd) {
+    __device__ __forceinline__ static float2 weight_a(float rr, float rb, float inv_rho, const StepParams& P) {
         if (P.precision_reference == 0) {
             float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * inv_rho;
             s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
             const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);  // a multiple of 2^-24
-            const float p0 = fmaf(-4.0f, pa, 1.0f - pa);              // 1 - 5 pa, exact
-            w0 = make_float2(p0, p0);
-            wa = make_float2(pa, pa);
-            wd = make_float2(0.25f * pa, 0.25f * pa);
-        } else {
-            w0 = make_float2(P.psi_r[0], P.psi_b[0]);
-            wa = make_float2(P.psi_r[1], P.psi_b[1]);
-            wd = make_float2(P.psi_r[2], P.psi_b[2]);
+            return make_float2(pa, pa);
         }
+        return make_float2(P.psi_r[1], P.psi_b[1]);
     }
 
-    // Reference pairs of window column t of a ring row whose copy has landed
-    // (the calling thread copied that column's densities itself).
+    // Axis reference pair of window column t of a ring row whose copy has
+    // landed (the calling thread copied that column's densities itself, and
+    // only it reads or writes them).
     __device__ __forceinline__ static void prep(char* slot, int t, const StepParams& P) {
-        const float2 rho = reinterpret_cast<const float2*>(slot)[t];
-        float2 w0, wa, wd;
-        weights(rho.x, rho.y, rcp(rho.x + rho.y), P, w0, wa, wd);
-        float2* ref = reinterpret_cast<float2*>(slot + kRhoBytes);
-        ref[t] = __fmul2_rn(rho, w0);
-        ref[kWin + t] = __fmul2_rn(rho, wa);
-        ref[2 * kWin + t] = __fmul2_rn(rho, wd);
+        float2* ref = reinterpret_cast<float2*>(slot);
+        const float2 rho = ref[t];
+        ref[t] = __fmul2_rn(rho, weight_a(rho.x, rho.y, rcp(rho.x + rho.y), P));
     }
 
-    // link class of link i: rest 0, axis 1 (even i), diagonal 2 (odd i)
-    __device__ __forceinline__ static constexpr int cls(int i) { return i == 0 ? 0 : ((i & 1) ? 2 : 1); }
+    // link class of link i >= 1: axis (even i) or diagonal (odd i)
+    __device__ __forceinline__ static constexpr bool diag(int i) { return (i & 1) != 0; }
+
     __device__ __forceinline__ static void pair(const char* slot, int i, int col, const StepParams& P, float& r,
                                                 float& b) {
-        const float2 ref = reinterpret_cast<const float2*>(slot + kRhoBytes)[cls(i) * kWin + col];
-        const H d = reinterpret_cast<const H*>(slot + kDevOff + i * kDevBytes)[col];
-        // (R_i, B_i) = (rho'_R psi^R_i, rho'_B psi^B_i) + d_i as one packed FP32x2 FMA
-        // (the stored deviation times 2^-k, exact, plus the reference, rounded once)
-        const float2 c = __ffma2_rn(to2(d), make_float2(P.dev_unscale, P.dev_unscale), ref);
+        if (i == 0) {
+            const float2 z = reinterpret_cast<const float2*>(slot + kRefBytes)[col];
+            r = z.x;
+            b = z.y;
+            return;
+        }
+        const float2 refa = reinterpret_cast<const float2*>(slot)[col];
+        const H* pairs = reinterpret_cast<const H*>(slot + kPairOff);
+        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale);
+        const float2 d = to2(pairs[(3 + i) * kWin + col]);
+        // reference pair plus the stored deviation times 2^-k (exact), rounded once
+        float2 c;
+        if (diag(i)) c = __ffma2_rn(refa, make_float2(0.25f, 0.25f), __fmul2_rn(d, un2));
+        else c = __ffma2_rn(d, un2, refa);
+        const float2 D = to2(pairs[dip_index(i) * kWin + col]);
+        c = dip_neg(i) ? __ffma2_rn(D, make_float2(-1.0f, -1.0f), c) : __fadd2_rn(c, D);
         r = c.x;
         b = c.y;
     }
 
+    // (ux, uy): the node's post-collision velocity, for the dipoles.
     __device__ __forceinline__ static void store(char* dst, size_t nodes, size_t node, const float (&fp)[9],
-                                                 float rr, float rb, float inv_rho, float sx, float sy,
-                                                 const StepParams& P) {
-        // everything scaled by 2^k (dev_scale) before rounding to 16 bits: a
-        // power-of-two factor commutes exactly with every FP32 operation below
+                                                 float rr, float rb, float inv_rho, float sx, float sy, float ux,
+                                                 float uy, const StepParams& P) {
+        // The recoloured pair of link i is (rho_C / rho) f+_i +/- s_i (Eq.
+        // eq_re_color); the record keeps it minus the dipole and the reference,
+        // scaled by 2^k (dev_scale) before rounding to 16 bits (a power-of-two
+        // factor commutes exactly with FP32 rounding).
         const float S = P.dev_scale;
+        H* pairs = reinterpret_cast<H*>(dst + nodes * 16) + node;
+        float2 D[4];
+        dipoles16(rr, rb, ux, uy, sx, sy, D);
+        float2 Dq[4];  // as stored, and as the decoder will use them
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const H h = from2x(D[j]);
+            pairs[j * nodes] = h;
+            Dq[j] = to2(h);
+        }
         float seg[9];
         segregation(sx * S, sy * S, seg);
-        H* dev = reinterpret_cast<H*>(dst + nodes * 8) + node;
-        const float aR = rr * inv_rho, aB = rb * inv_rho;
-        float2 w[3];
-        weights(rr, rb, inv_rho, P, w[0], w[1], w[2]);
-        // the stored densities absorb the rounding of the deviations, so that the
-        // decoded populations of the record sum to rho_R and rho_B (colour mass is
-        // conserved as with FP32 storage): rho'_C = rho_C - sum_i round(d_C,i)
-        // packed FP32x2 arithmetic on the (red, blue) pair of each link, lane by
-        // lane the same roundings as the scalar form
-        float2 e = make_float2(0.0f, 0.0f);
-        const float2 a2 = make_float2(aR * S, aB * S), mrho = make_float2(-rr * S, -rb * S);
-        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale);
+        const float2 rho2 = make_float2(rr, rb);
+        const float2 wa = weight_a(rr, rb, inv_rho, P);
+        const float2 wd = __fmul2_rn(wa, make_float2(0.25f, 0.25f));  // exact
+        const float2 refa = __fmul2_rn(rho2, wa);                     // the decoder's axis reference pair
+        const float2 a2 = make_float2(rr * inv_rho * S, rb * inv_rho * S), mrho = make_float2(-rr * S, -rb * S);
+        const float2 mS = make_float2(-S, -S), pS = make_float2(S, S), m1 = make_float2(-1.0f, -1.0f);
+        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale), q2 = make_float2(0.25f, 0.25f);
+        // The rest populations are what is left of rho_R and rho_B after the
+        // moving links as the decoder will see them (pair(), bit for bit), so
+        // that every record decodes to exactly its colour densities: colour mass
+        // is conserved through the storage to the rounding of that sum.
+        float2 sum = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float2 C = __ffma2_rn(a2, make_float2(fp[i], fp[i]), make_float2(seg[i], -seg[i]));
-            const H h = from2x(__ffma2_rn(mrho, w[cls(i)], C));
-            e = __ffma2_rn(to2(h), un2, e);
-            dev[i * nodes] = h;
+        for (int i = 1; i < 9; ++i) {
+            float2 C = __ffma2_rn(a2, make_float2(fp[i], fp[i]), make_float2(seg[i], -seg[i]));
+            const float2 Dj = Dq[dip_index(i)];
+            C = __ffma2_rn(Dj, dip_neg(i) ? pS : mS, C);
+            const H h = from2x(__ffma2_rn(mrho, diag(i) ? wd : wa, C));
+            pairs[(3 + i) * nodes] = h;
+            const float2 d = to2(h);
+            float2 c = diag(i) ? __ffma2_rn(refa, q2, __fmul2_rn(d, un2)) : __ffma2_rn(d, un2, refa);
+            c = dip_neg(i) ? __ffma2_rn(Dj, m1, c) : __fadd2_rn(c, Dj);
+            sum = __fadd2_rn(sum, c);
         }
-        reinterpret_cast<float2*>(dst)[node] = make_float2(rr - e.x, rb - e.y);
+        float2* own = reinterpret_cast<float2*>(dst) + node;
+        own[0] = rho2;
+        own[nodes] = __ffma2_rn(sum, m1, rho2);
     }
 };
 
@@ -706,7 +751,9 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                 const float ey = -R.nh(yd, 1)[t];
                 const float phim = fmaf(P.kphi_r, rr, P.kphi_b * rb) * inv_rho;
                 const float sg = P.beta * (rr * rb) * inv_rho * phim;
-                L::store(dst, nodes, static_cast<size_t>(yd) * nx + gxo, fp, rr, rb, inv_rho, sg * ex, sg * ey, P);
+                // post-collision velocity u + G / (2 rho) (the 16-bit record's dipoles)
+                L::store(dst, nodes, static_cast<size_t>(yd) * nx + gxo, fp, rr, rb, inv_rho, sg * ex, sg * ey,
+                         fmaf(0.5f * Gx, inv_rho, ux), fmaf(0.5f * Gy, inv_rho, uy), P);
             } else if (MODE == Pass::Fields) {
                 const size_t o = static_cast<size_t>(yd) * nx + gxo;
                 if (fo.rho_r) fo.rho_r[o] = rr;
