@@ -1649,8 +1649,9 @@ const char* cmrt_batch_last_error(const cmrt_batch* h) {
 namespace {
 
 // Grows the adjoint workspace: scratch planes, partial sums, two adjoint
-// states, `ckpt` checkpoint states and `seg` recomputed segment states.
-cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
+// states, `ckpt` checkpoint states, `seg` recomputed segment states and,
+// where the reverse step runs fused, `fields` sets of forward fields.
+cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg, size_t fields) {
     const size_t n = cells(*c);
     const size_t state = 18 * n * sizeof(float);
     auto grow = [&](void** ptr, size_t bytes) -> cmrt_status {
@@ -1688,10 +1689,10 @@ cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg) {
         if ((st = grow(reinterpret_cast<void**>(&c->adj_seg), seg * state))) return st;
         c->adj_seg_cap = seg;
     }
-    // Forward fields of the segment states the replay passes through (all
-    // but the last), where the reverse step runs fused.  Optional: without
-    // the memory for them the reverse steps recompute the fields.
-    const size_t nfields = cmrt::adj_fused(c->sp) && seg > 1 ? seg - 1 : 0;
+    // Forward fields of the states whose reverse step can read them, where the
+    // reverse step runs fused.  Optional: without the memory for them the
+    // reverse steps recompute the fields.
+    const size_t nfields = cmrt::adj_fused(c->sp) ? fields : 0;
     if (nfields > c->adj_fields_cap) {
         const size_t fstate = static_cast<size_t>(cmrt::kFwdPlanes) * n * sizeof(float);
         CK(c, cudaStreamSynchronize(c->stream));
@@ -1734,7 +1735,7 @@ extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* 
     if (!lam_next || !lam) return fail(c, CMRT_EINVAL, "lam_next and lam must not be NULL");
     if (c->p.precision != 0) return fail(c, CMRT_EINVAL, "the adjoint needs FP32 storage (precision 0)");
     if (set_device(c) != CMRT_OK) return CMRT_ECUDA;
-    cmrt_status st = ensure_adj(c, 0, 0);
+    cmrt_status st = ensure_adj(c, 0, 0, 0);
     if (st != CMRT_OK) return st;
     const size_t n18 = cells(*c) * 18;
     const float* src = lam_next;
@@ -1832,7 +1833,9 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     const int64_t K = ckpt_every;
     const size_t nck = static_cast<size_t>((nsteps + K - 1) / K);
     const size_t seg = static_cast<size_t>(std::min<int64_t>(K, nsteps));
-    cmrt_status st = ensure_adj(c, nck, seg);
+    // fields: of every state with every state kept, else of a segment's
+    // states but its last
+    cmrt_status st = ensure_adj(c, nck, seg, K == 1 ? static_cast<size_t>(nsteps) : seg - 1);
     if (st != CMRT_OK) return st;
     const size_t n = cells(*c), n18 = 18 * n;
     const size_t state = n18 * sizeof(float);
@@ -1845,15 +1848,27 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if ((st = adj_zero(c)) != CMRT_OK) return st;
     // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
     CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
+    // every state kept, and the field buffer holds the forward fields of all
+    // of them: each forward step writes those of the state it reads
+    const bool emit_all = K == 1 && c->adj_fields && cmrt::adj_fused(c->sp) &&
+                          c->adj_fields_cap >= static_cast<size_t>(nsteps);
+    const size_t nf = static_cast<size_t>(cmrt::kFwdPlanes) * n;
     if (K == 1) {
         // every state is kept (memory permitting, the cheapest sweep): step t
         // reads slot t of the checkpoint array and writes slot t + 1 (the last
         // step the lattice's other buffer), so that the reverse sweep reads
         // each state in place -- no copies and no recomputation
         for (int64_t t = 0; t < nsteps; ++t) {
+            float* src = c->adj_ckpt + static_cast<size_t>(t) * n18;
             void* dst = t + 1 < nsteps ? static_cast<void*>(c->adj_ckpt + static_cast<size_t>(t + 1) * n18)
                                        : c->buf[c->cur ^ 1];
-            STEP(c, c->adj_ckpt + static_cast<size_t>(t) * n18, dst);
+            if (emit_all) {
+                CK(c, cmrt::launch_step_fields(src, static_cast<float*>(dst), c->sp, c->rows, c->d_flag,
+                                               c->adj_fields + static_cast<size_t>(t) * nf, c->stream));
+                c->launches++;
+            } else {
+                STEP(c, src, dst);
+            }
             c->t++;
         }
         c->cur ^= 1;
@@ -1877,8 +1892,9 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if (K == 1) {
         for (int64_t t = nsteps - 1; t >= 0; --t, a ^= 1)
             CK(c, cmrt::launch_adjoint_step(c->adj_ckpt + static_cast<size_t>(t) * n18, c->adj_lam[a], c->sp,
-                                            c->adj_scratch, c->adj_partials, c->adj_lam[a ^ 1], c->stream));
-        c->launches += nsteps * cmrt::adj_launches_per_step(c->sp);
+                                            c->adj_scratch, c->adj_partials, c->adj_lam[a ^ 1], c->stream,
+                                            emit_all ? c->adj_fields + static_cast<size_t>(t) * nf : nullptr));
+        c->launches += nsteps * (cmrt::adj_launches_per_step(c->sp) - (emit_all ? 1 : 0));
     }
     for (int64_t k = static_cast<int64_t>(nck) - 1; K > 1 && k >= 0; --k) {
         const int64_t len = std::min((k + 1) * K, nsteps) - k * K;

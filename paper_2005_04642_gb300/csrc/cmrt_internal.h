@@ -77,12 +77,12 @@ struct FieldOut {
 };
 
 // The forward fields of a state that one reverse step of the adjoint reads,
-// as planes: colour densities, momentum, colour fractions, Phi', grad rho^N,
-// K, the force G and the force-adjusted velocity u (the first planes of the
+// as planes: colour densities, colour fractions, Phi', grad rho^N, K, the
+// force G and the force-adjusted velocity u (the first planes of the
 // adjoint's scratch, and the layout Pass::StepFields writes).
 enum FwdPlane : int {
-    kFwdRR = 0, kFwdRB, kFwdJX, kFwdJY, kFwdCHR, kFwdCHB, kFwdPHIP, kFwdGX, kFwdGY, kFwdK, kFwdGFX, kFwdGFY, kFwdUX,
-    kFwdUY, kFwdPlanes
+    kFwdRR = 0, kFwdRB, kFwdCHR, kFwdCHB, kFwdPHIP, kFwdGX, kFwdGY, kFwdK, kFwdGFX, kFwdGFY, kFwdUX, kFwdUY,
+    kFwdPlanes
 };
 
 // Geometry of the fused row-marching kernel: a CTA owns a strip of kTileX

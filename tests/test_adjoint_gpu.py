@@ -195,10 +195,10 @@ def test_fused_kernels_equal_plane_passes(wall):
 @pytest.mark.parametrize("fused,wall", [(2, False), (1, False), (1, True)], ids=["planes", "fused", "fused_walls"])
 def test_checkpoint_interval_gives_identical_gradients(fused, wall):
     """Every checkpoint interval gives the same objective and gradients, bit
-    for bit.  With the fused reverse step, K = 1 recomputes every state's
-    forward fields in the reverse step, while K > 1 takes them from the
-    replayed steps that wrote them (all but a segment's last state): the two
-    sources must agree exactly."""
+    for bit.  With the fused reverse step the forward fields of a state come
+    from the forward step that read it (every state with K = 1, all but a
+    segment's last with K > 1) or are recomputed by the reverse step (a
+    segment's last state): the two sources must agree exactly."""
     nsteps = 12
     d, rn0, u0, target = _drop_setup(32, 8.0, nsteps, g=1e-4, wall=wall)
     d["adjoint_fused"] = fused
@@ -214,9 +214,11 @@ def test_checkpoint_interval_gives_identical_gradients(fused, wall):
         assert J == outs[0][0]
         assert g == outs[0][1]
         assert np.array_equal(grn, outs[0][2])
-    # one segment of 12 replays 11 steps; where they write the forward fields,
-    # 11 reverse steps skip their recomputation (one launch each)
-    assert launches[12] - launches[1] == (0 if fused == 1 else 11)
+    # one segment of 12 replays 11 steps.  Fused, every forward step writes the
+    # forward fields its reverse step reads -- with every state kept all 12,
+    # in the segment the 11 replayed ones -- so K = 12 runs one forward-field
+    # recomputation more; the plane passes recompute them in every reverse step
+    assert launches[12] - launches[1] == (12 if fused == 1 else 11)
 
 
 def test_recorded_segment_graphs_are_replayed_exactly():

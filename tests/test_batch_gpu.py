@@ -66,6 +66,21 @@ def test_members_bit_identical_to_single_lattices(graph_steps):
     b.close()
 
 
+@pytest.mark.parametrize("precision", [2, 1], ids=["fp16", "bf16"])
+def test_16bit_members_bit_identical_to_single_lattices(precision):
+    """The 16-bit record (dipoles, deviations, exact rest populations) in the
+    persistent batched kernel: every member equal to the same lattice
+    stepped alone, record for record."""
+    members = [(dict(d, precision=precision), rn, u) for d, rn, u in _mixed_members(seed=13)]
+    b = cm.Batch(members)
+    b.step(6)
+    for k, m in enumerate(members):
+        got = b.member(k).populations()
+        ref = _alone(m, 6)
+        assert torch.equal(got, ref), f"member {k} ({m[0]['nx']}x{m[0]['ny']})"
+    b.close()
+
+
 def test_rows_and_tiling_do_not_change_results():
     members = _mixed_members(seed=12)
     a = cm.Batch(members)
