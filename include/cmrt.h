@@ -115,11 +115,14 @@ typedef struct {
                                 1 = the lattice weights w_i; 2 = phi_i of the pure colour C  */
     int32_t adjoint_fused;   /* kernels of one reverse step of cmrt_adjoint / cmrt_step_vjp
                                 (compact stencil; App. B's stencil always uses plane passes):
-                                0 = automatic -- two fused row-wavefront kernels where the lattice
-                                fills 16-row segments in two waves of the GPU, eight per-node
-                                plane passes on smaller lattices; 1 = always the fused kernels;
-                                2 = always the plane passes.  Both compute the same values
-                                (rounding order aside)                                          */
+                                0 = automatic -- in cmrt_adjoint the fused kernels whenever its
+                                forward steps can write the forward fields the reverse steps read
+                                (one set of 12 planes per recomputed or kept state, allocated where
+                                memory allows); otherwise, and in cmrt_step_vjp, the fused kernels
+                                where the lattice fills 16-row segments in two waves of the GPU and
+                                eight per-node plane passes on smaller lattices; 1 = always the
+                                fused kernels; 2 = always the plane passes.  Both compute the same
+                                values (rounding order aside)                                     */
 } cmrt_params;
 
 /* ABI version of the loaded library (CMRT_ABI_VERSION). */

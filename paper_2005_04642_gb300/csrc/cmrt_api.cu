@@ -74,6 +74,7 @@ struct Ctx {
     struct AdjGraph {
         int64_t len;
         int a;
+        bool fields;       // the replayed steps write the forward fields
         cudaGraphExec_t exec;
         int64_t launches;  // kernels one replay of the graph launches
     };
@@ -1692,7 +1693,7 @@ cmrt_status ensure_adj(Ctx* c, size_t ckpt, size_t seg, size_t fields) {
     // Forward fields of the states whose reverse step can read them, where the
     // reverse step runs fused.  Optional: without the memory for them the
     // reverse steps recompute the fields.
-    const size_t nfields = cmrt::adj_fused(c->sp) ? fields : 0;
+    const size_t nfields = cmrt::adj_fields_usable(c->sp) ? fields : 0;
     if (nfields > c->adj_fields_cap) {
         const size_t fstate = static_cast<size_t>(cmrt::kFwdPlanes) * n * sizeof(float);
         CK(c, cudaStreamSynchronize(c->stream));
@@ -1767,16 +1768,18 @@ extern "C" cmrt_status cmrt_step_vjp(cmrt_ctx* h, const float* lam_next, float* 
 // of state j, bit for bit those the reverse step would recompute, so that
 // reverse steps len - 2 .. 0 skip that recomputation.  Recorded on the first
 // use of (len, a) -- on a private stream, so the caller's stream may be any
-// -- and replayed afterwards; *launches receives its kernel count.
-cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out, int64_t* launches) {
+// -- and replayed afterwards; *launches receives its kernel count.  sp: the
+// call's parameters (fused reverse kernels where it uses forward fields).
+cmrt_status adj_segment_graph(Ctx* c, const cmrt::StepParams& sp, int64_t len, int a, cudaGraphExec_t* out,
+                              int64_t* launches) {
+    const bool emit = c->adj_fields && cmrt::adj_fused(sp) && len > 1 &&
+                      static_cast<size_t>(len - 1) <= c->adj_fields_cap;
     for (const Ctx::AdjGraph& g : c->adj_graphs)
-        if (g.len == len && g.a == a) {
+        if (g.len == len && g.a == a && g.fields == emit) {
             *out = g.exec;
             *launches = g.launches;
             return CMRT_OK;
         }
-    const bool emit = c->adj_fields && cmrt::adj_fused(c->sp) && len > 1 &&
-                      static_cast<size_t>(len - 1) <= c->adj_fields_cap;
     const size_t nf = static_cast<size_t>(cmrt::kFwdPlanes) * cells(*c);
     auto fields = [&](int64_t j) { return c->adj_fields + static_cast<size_t>(j) * nf; };
     int64_t count = 0;
@@ -1790,7 +1793,7 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out, 
     if (e == cudaSuccess) {
         for (int64_t j = 1; j < len && e == cudaSuccess; ++j) {
             if (emit) {
-                e = cmrt::launch_step_fields(slot(j - 1), slot(j), c->sp, c->rows, c->d_flag, fields(j - 1),
+                e = cmrt::launch_step_fields(slot(j - 1), slot(j), sp, c->rows, c->d_flag, fields(j - 1),
                                              c->stream);
                 count += 1;
             } else {
@@ -1800,9 +1803,9 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out, 
         int aa = a;
         for (int64_t j = len - 1; j >= 0 && e == cudaSuccess; --j, aa ^= 1) {
             const float* fwd = emit && j < len - 1 ? fields(j) : nullptr;
-            e = cmrt::launch_adjoint_step(slot(j), c->adj_lam[aa], c->sp, c->adj_scratch, c->adj_partials,
+            e = cmrt::launch_adjoint_step(slot(j), c->adj_lam[aa], sp, c->adj_scratch, c->adj_partials,
                                           c->adj_lam[aa ^ 1], c->stream, fwd);
-            count += cmrt::adj_launches_per_step(c->sp) - (fwd ? 1 : 0);
+            count += cmrt::adj_launches_per_step(sp) - (fwd ? 1 : 0);
         }
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(c->adj_capture, &g);
@@ -1812,7 +1815,7 @@ cmrt_status adj_segment_graph(Ctx* c, int64_t len, int a, cudaGraphExec_t* out, 
     }
     c->stream = user;
     if (e != cudaSuccess) return fail(c, CMRT_ECUDA, "recording the adjoint segment graph failed: %s", cudaGetErrorString(e));
-    c->adj_graphs.push_back({len, a, exec, count});
+    c->adj_graphs.push_back({len, a, emit, exec, count});
     *out = exec;
     *launches = count;
     return CMRT_OK;
@@ -1848,10 +1851,16 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     if ((st = adj_zero(c)) != CMRT_OK) return st;
     // forward, keeping P_{kK-1} (relative to the current time) as checkpoint k
     CK(c, cudaMemcpyAsync(c->adj_ckpt, c->buf[c->cur], state, cudaMemcpyDeviceToDevice, c->stream));
-    // every state kept, and the field buffer holds the forward fields of all
-    // of them: each forward step writes those of the state it reads
-    const bool emit_all = K == 1 && c->adj_fields && cmrt::adj_fused(c->sp) &&
-                          c->adj_fields_cap >= static_cast<size_t>(nsteps);
+    // Forward fields from the forward steps where the field buffer could be
+    // had: then every reverse step of the call runs fused (the same kernels
+    // whichever source a state's fields come from, so the checkpoint interval
+    // does not change the result); otherwise the lattice-size rule decides.
+    const size_t need = K == 1 ? static_cast<size_t>(nsteps) : seg - 1;
+    const bool use_fields = cmrt::adj_fields_usable(c->sp) && need > 0 && c->adj_fields && c->adj_fields_cap >= need;
+    cmrt::StepParams spa = c->sp;
+    if (use_fields) spa.adjoint_fused = 1;
+    // every state kept: each forward step writes the fields of the state it reads
+    const bool emit_all = K == 1 && use_fields;
     const size_t nf = static_cast<size_t>(cmrt::kFwdPlanes) * n;
     if (K == 1) {
         // every state is kept (memory permitting, the cheapest sweep): step t
@@ -1891,10 +1900,10 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
     // and runs its reverse steps
     if (K == 1) {
         for (int64_t t = nsteps - 1; t >= 0; --t, a ^= 1)
-            CK(c, cmrt::launch_adjoint_step(c->adj_ckpt + static_cast<size_t>(t) * n18, c->adj_lam[a], c->sp,
+            CK(c, cmrt::launch_adjoint_step(c->adj_ckpt + static_cast<size_t>(t) * n18, c->adj_lam[a], spa,
                                             c->adj_scratch, c->adj_partials, c->adj_lam[a ^ 1], c->stream,
                                             emit_all ? c->adj_fields + static_cast<size_t>(t) * nf : nullptr));
-        c->launches += nsteps * (cmrt::adj_launches_per_step(c->sp) - (emit_all ? 1 : 0));
+        c->launches += nsteps * (cmrt::adj_launches_per_step(spa) - (emit_all ? 1 : 0));
     }
     for (int64_t k = static_cast<int64_t>(nck) - 1; K > 1 && k >= 0; --k) {
         const int64_t len = std::min((k + 1) * K, nsteps) - k * K;
@@ -1902,7 +1911,7 @@ extern "C" cmrt_status cmrt_adjoint(cmrt_ctx* h, int64_t nsteps, int32_t ckpt_ev
                               c->stream));
         cudaGraphExec_t exec = nullptr;
         int64_t nl = 0;
-        if ((st = adj_segment_graph(c, len, a, &exec, &nl)) != CMRT_OK) return st;
+        if ((st = adj_segment_graph(c, spa, len, a, &exec, &nl)) != CMRT_OK) return st;
         CK(c, cudaGraphLaunch(exec, c->stream));
         c->launches += nl;
         a ^= static_cast<int>(len & 1);

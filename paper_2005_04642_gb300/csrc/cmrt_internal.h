@@ -178,6 +178,10 @@ cudaError_t launch_adjoint_step(const float* post, const float* lam_post, const 
                                 double* partials, float* lam_prev, cudaStream_t s, const float* fwd = nullptr);
 // whether one reverse step runs as the fused kernels (compact stencil, lattice large enough or asked for)
 bool adj_fused(const StepParams& P);
+// whether the fused kernels may read forward fields written by the forward
+// steps (compact stencil, plane passes not asked for); a call that uses such
+// fields runs all its reverse steps fused
+bool adj_fields_usable(const StepParams& P);
 // same, but writes dJ/df(t) (pre-collision, float[2][9][ny][nx]) into lam_pre
 cudaError_t launch_adjoint_step_pre(const float* post, const float* lam_post, const StepParams& P, float* scratch,
                                     double* partials, float* lam_pre, cudaStream_t s);

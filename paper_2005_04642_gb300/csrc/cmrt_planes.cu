@@ -1437,6 +1437,7 @@ cudaError_t launch_diag_planes(const float* post, const StepParams& P, float* sc
 }
 
 bool adj_fused(const StepParams& P) { return P.stencil_order == 2 && use_fused(P); }
+bool adj_fields_usable(const StepParams& P) { return P.stencil_order == 2 && P.adjoint_fused != 2; }
 
 int adj_launches_per_step(const StepParams& P) {
     if (adj_fused(P)) return 3;  // fused forward fields, collision pass, fused tail
