@@ -93,6 +93,27 @@ def test_static_drop_100_steps(prec):
     assert abs(m1["mass_b"] - m0["mass_b"]) / m0["mass_b"] <= 1e-6
 
 
+@pytest.mark.parametrize("prec", [FP16, BF16])
+@pytest.mark.parametrize("nx,ny,wall", [(130, 140, True), (33, 17, False), (250, 36, False)],
+                         ids=["walls130x140", "ragged33x17", "ragged250x36"])
+def test_ragged_lattices_100_steps(prec, nx, ny, wall):
+    """Widths that are not a multiple of 4 (each thread copies its own column
+    of every plane, no 16-byte chunks), strips that end inside a window, and
+    walls: a drop with a velocity field, 100 steps against the FP64 oracle at
+    the 16-bit bars."""
+    d = I.base_params(nx, ny, rho0_r=1.0, rho0_b=0.1, sigma=0.01, wall_y=wall, g_acc=(1e-5, -1e-5))
+    r = max(3.0, min(nx, ny) / 4.0)
+    rn = I.drops_field(nx, ny, [(nx / 2.0 + 0.3, ny / 2.0 - 0.2)], [r], periodic_y=not wall)
+    u = I.velocity_noise(nx, ny, 1e-3, 21)
+    p = _oracle_params(d)
+    R, B = O.run(*O.init_state(rn, u[0], u[1], p), p, 100)
+    lat = cm.Lattice(dict(d, precision=prec), rn, u)
+    lat.step(100)
+    errs = _field_errs(lat, p, R, B)
+    lat.close()
+    _check(errs, prec)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("prec", [FP16, BF16])
 def test_buoyant_replica_2000_steps(prec):
