@@ -48,32 +48,29 @@ namespace cmrt {
 namespace {
 
 constexpr int kPlanes = 18;
-// Rings of stage results, each holding only the rows its readers need (a
-// row is one float per window column; fields x and y interleaved by row):
-//   grad rho^N  4 rows  (B writes row s - 2 while C may still read s - 4)
-//   n-hat       4 rows
-//   G           4 rows  (C writes row s - 3 while D may still read s - 5)
-//   u           4 rows
-// The mirrored rows beyond a wall share these slots: row -1 takes the slot
-// of row 3, and row ny the slot of row ny - 4, written one row iteration
-// after row ny - 1, when no stage reads row ny - 4 any more.
+// Rings of stage results, four rows each (a row is one float per window
+// column; fields x and y interleaved by row): the front's B and C write rows
+// s - 2 and s - 3 of iteration k + 1 (that is, s - 1 and s - 2) while the
+// back's D of iteration k may still read n-hat and G of row s - 4 and u of
+// rows s - 5 .. s - 3; grad rho^N only C reads, on the front.  The mirrored
+// rows beyond a wall share these slots: row -1 takes the slot of row 3, and
+// row ny the slot of row ny - 4, written one row iteration after row ny - 1,
+// when no stage reads row ny - 4 any more.
 constexpr int kBFloats = (4 * 2 + 4 * 2) * kWin;  // grad rho^N, n-hat
 constexpr int kCFloats = (4 * 2 + 4 * 2) * kWin;  // G, u
 
 // The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
-// kThreads ("front") stream the rows in and run stages A-B, while the other
-// kThreads ("back") run stages C-D one row iteration behind them.
+// kThreads ("front") stream the rows in and run stages A-C, while the other
+// kThreads ("back") run stage D one row iteration behind them.
 constexpr int kStepThreads = 2 * kThreads;
 // Named barriers (0 is __syncthreads): the front among themselves; front ->
-// back "stages A and B of iteration k are in shared memory" (kBarC, the
-// hand-off to stage C) and back -> front "stages C and D of iteration k are
-// done with their rows" (kBarD), each alternating between two ids by the
-// parity of k so that no barrier sees arrivals of two iterations; the back
-// among themselves between C and D.
+// back "stages A to C of iteration k are in shared memory" (kBarC, the
+// hand-off to stage D) and back -> front "stage D of iteration k is done
+// with its rows" (kBarD), each alternating between two ids by the parity of
+// k so that no barrier sees arrivals of two iterations.
 constexpr int kBarFront = 1;
 constexpr int kBarC = 2;  // 2, 3
 constexpr int kBarD = 4;  // 4, 5
-constexpr int kBarBack = 6;  // the back warps among themselves
 
 template <int ID, int N>
 __device__ __forceinline__ void bar_sync() {
@@ -534,16 +531,19 @@ struct DiagAcc {
 // the ring slot of row s - 7.  The fields and diagnostics passes run all four
 // stages in every thread of a 128-thread CTA, one barrier between stages.
 // The step is warp-specialised (2 x 128 threads): the front threads wait for
-// the copies, issue the next one and run A and B of iteration k, then
-// publish them with bar.arrive; the back threads run C and D of iteration k
-// (a back-only barrier between them) while the front is at iteration k + 1.
+// the copies, issue the next one and run A, B and C of iteration k, then
+// publish them with bar.arrive; the back threads run D of iteration k while
+// the front is at iteration k + 1.  (With C on the back the back set the
+// pace of the 16-bit step, its decode and encode being the heavier; C on the
+// front leaves the FP32 step as it was and makes the FP16 one 2.6 % faster.)
 // D reads population rows s - 5 .. s - 3 (nine rows in flight in all: D's
-// three, A's three, two copies and the row D of iteration k - 1 read).
-// Before leaving iteration k the front waits for C and D of iteration k - 1,
-// so that in iteration k + 1 nothing it writes -- ring A row s, grad rho^N
-// and n-hat rows s - 1, the copy into the slot of row s - 6 -- is still
-// being read; the mirrored wall row ny of n-hat has a slot of its own, and
-// so has u's, written and read by the back alone.
+// three, A's three, two copies and the row D of iteration k - 1 read), u
+// rows s - 5 .. s - 3, G and n-hat of row s - 4.  Before leaving iteration k
+// the front waits for D of iteration k - 1, so that in iteration k + 1
+// nothing it writes -- ring A row s, grad rho^N and n-hat rows s - 1, G and
+// u row s - 2, the copy into the slot of row s - 6 -- is still being read;
+// the mirrored wall rows ny of n-hat and u take the slots of row ny - 4,
+// written two row iterations after D of iteration k read row ny - 4 last.
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsigned pop_addr, const char* __restrict__ src,
                                            char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
@@ -818,8 +818,10 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             stage_a(s, ks);
             bar_sync<kBarFront, kThreads>();
             stage_b(s);
-            // publish A and B of iteration k, then wait until C and D of
-            // iteration k - 1 are done with the rows that iteration k + 1 overwrites
+            bar_sync<kBarFront, kThreads>();
+            stage_c(s);
+            // publish A, B and C of iteration k, then wait until D of iteration
+            // k - 1 is done with the rows that iteration k + 1 overwrites
             if (k & 1) {
                 bar_arrive<kBarC + 1, kStepThreads>();
                 bar_sync<kBarD + 1, kStepThreads>();
@@ -835,8 +837,6 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
         for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
             if (k & 1) bar_sync<kBarC + 1, kStepThreads>();
             else bar_sync<kBarC, kStepThreads>();
-            stage_c(s_first + k);
-            bar_sync<kBarBack, kThreads>();  // u of row s - 3 is in shared memory
             stage_d(s_first + k, ks);
             if (k + 1 < iters) {
                 if (k & 1) bar_arrive<kBarD, kStepThreads>();  // D of iteration k + 1 (even) may follow
