@@ -79,10 +79,13 @@ struct FieldOut {
 // The forward fields of a state that one reverse step of the adjoint reads,
 // as planes: colour densities, colour fractions, Phi', grad rho^N, K, the
 // force G and the force-adjusted velocity u (the first planes of the
-// adjoint's scratch, and the layout Pass::StepFields writes).
+// adjoint's scratch, and the layout Pass::StepFields writes).  The momentum
+// planes between them are holes in a set the step writes (the plane passes
+// use them): with the twelve planes packed the reverse collision pass ran
+// 4 % slower at 2048^2, measured, so the sets keep these offsets.
 enum FwdPlane : int {
-    kFwdRR = 0, kFwdRB, kFwdCHR, kFwdCHB, kFwdPHIP, kFwdGX, kFwdGY, kFwdK, kFwdGFX, kFwdGFY, kFwdUX, kFwdUY,
-    kFwdPlanes
+    kFwdRR = 0, kFwdRB, kFwdJX, kFwdJY, kFwdCHR, kFwdCHB, kFwdPHIP, kFwdGX, kFwdGY, kFwdK, kFwdGFX, kFwdGFY, kFwdUX,
+    kFwdUY, kFwdPlanes
 };
 
 // Geometry of the fused row-marching kernel: a CTA owns a strip of kTileX

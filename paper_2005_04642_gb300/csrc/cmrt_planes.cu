@@ -49,7 +49,7 @@ constexpr int kAT = 128;  // threads per CTA (along x)
 
 // Scratch planes, each float[ny][nx].
 enum Plane : int {
-    kRR = 0, kRB, kCHR, kCHB, kPHIP, kGX, kGY, kK, kGFX, kGFY, kUX, kUY, kJX, kJY,  // forward
+    kRR = 0, kRB, kJX, kJY, kCHR, kCHB, kPHIP, kGX, kGY, kK, kGFX, kGFY, kUX, kUY,  // forward
     kFB0,                                                                   // 9 planes f-bar
     kRRB = kFB0 + 9, kRBB, kUXB, kUYB, kGFXB, kGFYB, kDPXB, kDPYB, kDIVUB, kGXB, kGYB, kRNB, kJXB, kJYB, kKB,
     kNumPlanes
@@ -57,9 +57,8 @@ enum Plane : int {
 static_assert(kNumPlanes == kAdjPlanes, "scratch plane count");
 static_assert(kRR == kFwdRR && kRB == kFwdRB && kCHR == kFwdCHR && kCHB == kFwdCHB && kPHIP == kFwdPHIP &&
                   kGX == kFwdGX && kGY == kFwdGY && kK == kFwdK && kGFX == kFwdGFX && kGFY == kFwdGFY &&
-                  kUX == kFwdUX && kUY == kFwdUY && kJX == kFwdPlanes,
-              "the forward planes the reverse step reads lead the scratch planes, in the order the step "
-              "kernel writes them");
+                  kUX == kFwdUX && kJX == kFwdJX && kJY == kFwdJY && kFB0 == kFwdPlanes,
+              "the forward planes lead the scratch planes, in the order the step kernel writes them");
 
 // periodic image of v in [0, n); the integer modulo only for images more than
 // one period away (lattices narrower than a stencil's reach)

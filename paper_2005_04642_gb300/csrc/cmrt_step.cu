@@ -60,17 +60,20 @@ constexpr int kBFloats = (4 * 2 + 4 * 2) * kWin;  // grad rho^N, n-hat
 constexpr int kCFloats = (4 * 2 + 4 * 2) * kWin;  // G, u
 
 // The step runs warp-specialised: a CTA of 2 x kThreads threads, whose first
-// kThreads ("front") stream the rows in and run stages A-C, while the other
-// kThreads ("back") run stage D one row iteration behind them.
+// kThreads ("front") stream the rows in and run stages A and B, and C with
+// 16-bit storage, while the other kThreads ("back") run stage D, and C with
+// FP32 storage, one row iteration behind them.
 constexpr int kStepThreads = 2 * kThreads;
 // Named barriers (0 is __syncthreads): the front among themselves; front ->
-// back "stages A to C of iteration k are in shared memory" (kBarC, the
-// hand-off to stage D) and back -> front "stage D of iteration k is done
-// with its rows" (kBarD), each alternating between two ids by the parity of
-// k so that no barrier sees arrivals of two iterations.
+// back "the front's stages of iteration k are in shared memory" (kBarC) and
+// back -> front "the back's stages of iteration k are done with their rows"
+// (kBarD), each alternating between two ids by the parity of k so that no
+// barrier sees arrivals of two iterations; the back among themselves between
+// C and D.
 constexpr int kBarFront = 1;
 constexpr int kBarC = 2;  // 2, 3
 constexpr int kBarD = 4;  // 4, 5
+constexpr int kBarBack = 6;
 
 template <int ID, int N>
 __device__ __forceinline__ void bar_sync() {
@@ -132,6 +135,7 @@ __device__ __forceinline__ float2 sum9x2(const float (&r)[9], const float (&b)[9
 // 32-bit: 18 FP32 planes.
 struct LayoutF32 {
     static constexpr bool kPrep = false;
+    static constexpr bool kCFront = false;  // stage C on the back warps (see chain_tile)
     static constexpr int kSlotBytes = kPlanes * kWin * 4;
     static constexpr int kChunks = kSlotBytes / 16;
     static constexpr int kVecIters = (kChunks + kThreads - 1) / kThreads;
@@ -235,6 +239,7 @@ struct Layout16 {
     static constexpr int kPairChunks = kPairPlanes * kPairBytes / 16;
     static constexpr int kVecIters = (kPairChunks + kThreads - 1) / kThreads;
     static constexpr bool kPrep = true;
+    static constexpr bool kCFront = true;  // stage C on the front warps (see chain_tile)
     static constexpr size_t node_bytes() { return 16 + kPairPlanes * 4; }
 
     __device__ __forceinline__ static float2 to2(H v);
@@ -531,19 +536,24 @@ struct DiagAcc {
 // the ring slot of row s - 7.  The fields and diagnostics passes run all four
 // stages in every thread of a 128-thread CTA, one barrier between stages.
 // The step is warp-specialised (2 x 128 threads): the front threads wait for
-// the copies, issue the next one and run A, B and C of iteration k, then
-// publish them with bar.arrive; the back threads run D of iteration k while
-// the front is at iteration k + 1.  (With C on the back the back set the
-// pace of the 16-bit step, its decode and encode being the heavier; C on the
-// front leaves the FP32 step as it was and makes the FP16 one 2.6 % faster.)
+// the copies, issue the next one and run A and B of iteration k, then
+// publish them with bar.arrive; the back threads run C and D of iteration k
+// (a back-only barrier between them) while the front is at iteration k + 1.
+// With 16-bit storage C runs on the front instead: there the back, with its
+// decode and encode, sets the pace, and the move makes the step 2.6 %
+// faster; FP32 (Step and StepFields) keeps C on the back, which StepFields,
+// whose front also stores A's and B's forward fields, needs (5.6 % slower
+// otherwise) and the FP32 step does not mind.
 // D reads population rows s - 5 .. s - 3 (nine rows in flight in all: D's
 // three, A's three, two copies and the row D of iteration k - 1 read), u
-// rows s - 5 .. s - 3, G and n-hat of row s - 4.  Before leaving iteration k
-// the front waits for D of iteration k - 1, so that in iteration k + 1
-// nothing it writes -- ring A row s, grad rho^N and n-hat rows s - 1, G and
-// u row s - 2, the copy into the slot of row s - 6 -- is still being read;
-// the mirrored wall rows ny of n-hat and u take the slots of row ny - 4,
-// written two row iterations after D of iteration k read row ny - 4 last.
+// rows s - 5 .. s - 3, G and n-hat of row s - 4; C on the back also reads
+// n-hat rows s - 4 .. s - 2, grad rho^N and ring A of row s - 3.  Before
+// leaving iteration k the front waits for the back's iteration k - 1, so
+// that in iteration k + 1 nothing it writes -- ring A row s, grad rho^N and
+// n-hat rows s - 1, with C on the front G and u row s - 2, the copy into the
+// slot of row s - 6 -- is still being read; the mirrored wall rows ny of
+// n-hat and u take the slots of row ny - 4, written at least one row
+// iteration after the last stage that reads row ny - 4 has run.
 template <class L, bool VEC, bool WALLS, Pass MODE, bool PRE>
 __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsigned pop_addr, const char* __restrict__ src,
                                            char* __restrict__ dst, const StepParams& P, const int x0, const int y0,
@@ -551,6 +561,7 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
                                            DiagAcc& acc) {
     constexpr bool kStep = MODE == Pass::Step || MODE == Pass::StepFields;
     constexpr bool kWS = kStep;
+    constexpr bool kCFront = L::kCFront;
     const bool front = !kWS || threadIdx.x < kThreads;  // warp-uniform
     const int t = front ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) - kThreads;
     const int nx = P.nx, ny = P.ny;
@@ -818,10 +829,12 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
             stage_a(s, ks);
             bar_sync<kBarFront, kThreads>();
             stage_b(s);
-            bar_sync<kBarFront, kThreads>();
-            stage_c(s);
-            // publish A, B and C of iteration k, then wait until D of iteration
-            // k - 1 is done with the rows that iteration k + 1 overwrites
+            if (kCFront) {
+                bar_sync<kBarFront, kThreads>();
+                stage_c(s);
+            }
+            // publish the front's stages of iteration k, then wait until the back
+            // is done with iteration k - 1, whose rows iteration k + 1 overwrites
             if (k & 1) {
                 bar_arrive<kBarC + 1, kStepThreads>();
                 bar_sync<kBarD + 1, kStepThreads>();
@@ -837,6 +850,10 @@ __device__ __forceinline__ void chain_tile(const Rings<L, WALLS>& R, const unsig
         for (int k = 0; k < iters; ++k, ks = ring_next(ks)) {
             if (k & 1) bar_sync<kBarC + 1, kStepThreads>();
             else bar_sync<kBarC, kStepThreads>();
+            if (!kCFront) {
+                stage_c(s_first + k);
+                bar_sync<kBarBack, kThreads>();  // u of row s - 3 is in shared memory
+            }
             stage_d(s_first + k, ks);
             if (k + 1 < iters) {
                 if (k & 1) bar_arrive<kBarD, kStepThreads>();  // D of iteration k + 1 (even) may follow
