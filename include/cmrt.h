@@ -117,7 +117,7 @@ typedef struct {
                                 (compact stencil; App. B's stencil always uses plane passes):
                                 0 = automatic -- in cmrt_adjoint the fused kernels whenever its
                                 forward steps can write the forward fields the reverse steps read
-                                (one set of 12 planes per recomputed or kept state, allocated where
+                                (one set of 14 planes per recomputed or kept state, allocated where
                                 memory allows); otherwise, and in cmrt_step_vjp, the fused kernels
                                 where the lattice fills 16-row segments in two waves of the GPU and
                                 eight per-node plane passes on smaller lattices; 1 = always the
