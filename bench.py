@@ -403,16 +403,28 @@ def run_cmrt(args, rank, world, local_rank):
     h_out = [torch.empty((d["ny"], d["nx"]), dtype=torch.float32).pin_memory() for _ in range(5)]
     barrier()
     t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    th = [0.0] * 4
+    ev[0].record(stream)
     pr = cm.make_params(d)
     ctx = cm.cmrt_init(pr, h_rn.data_ptr(), h_u.data_ptr(), stream.cuda_stream)
+    ev[1].record(stream)
+    th[1] = time.perf_counter()
     cm.cmrt_step(ctx, args.steps)
+    ev[2].record(stream)
+    th[2] = time.perf_counter()
     cm.cmrt_fields(ctx, *(o.data_ptr() for o in h_out))
-    e1.record(stream)
+    ev[3].record(stream)
+    th[3] = time.perf_counter()
     barrier()
     e2e_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    # where the end-to-end time went: device time between the calls' events,
+    # and host time to each call's return (cmrt_init allocates the lattice)
+    e2e_phases = {"init_device_ms": ev[0].elapsed_time(ev[1]), "steps_device_ms": ev[1].elapsed_time(ev[2]),
+                  "fields_device_ms": ev[2].elapsed_time(ev[3]), "init_host_ms": (th[1] - t0) * 1e3,
+                  "steps_enqueue_host_ms": (th[2] - th[1]) * 1e3, "fields_host_ms": (th[3] - th[2]) * 1e3,
+                  "wall_ms": e2e_s * 1e3}
     cm.cmrt_destroy(ctx)
     e2e_value = whole_job_mlups(cells, args.steps, world, max_over_ranks(e2e_s, dist, "cuda"))
     h2d = (h_rn.numel() + h_u.numel()) * 4
@@ -441,7 +453,7 @@ def run_cmrt(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args.side), "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                    "d2h_bytes_per_step": d2h / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps, "phases": e2e_phases,
                     "what": "cmrt_init from pinned host rho^N_0, u_0 + K steps + cmrt_fields into pinned host buffers"},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "variants": variants,
             "check": {"mass_r": diag["mass_r"], "mass_b": diag["mass_b"], "nonfinite": diag["nonfinite"]}}
