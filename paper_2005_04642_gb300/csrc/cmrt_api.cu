@@ -63,9 +63,10 @@ struct Ctx {
     size_t adj_ckpt_cap = 0;
     float* adj_seg = nullptr;            // segment states (slot 0: the checkpoint), float[cap][18][n]
     size_t adj_seg_cap = 0;
-    // forward fields of segment states 0 .. cap - 1, written by the replayed
-    // steps for the reverse steps, float[cap][kFwdPlanes][n]; null where the
-    // reverse step recomputes them (plane passes, or no memory for them)
+    // forward fields of states 0 .. cap - 1 of a segment (written by the
+    // replayed steps) or of every kept state (written by the forward run), for
+    // the reverse steps, float[cap][kFwdPlanes][n]; null where the reverse
+    // step recomputes them (plane passes, or no memory for them)
     float* adj_fields = nullptr;
     size_t adj_fields_cap = 0;
     // CUDA graphs of one checkpoint segment (replay + reverse steps), keyed by
