@@ -57,8 +57,9 @@ extern "C" {
  * step graphs (cmrt_set_graph_steps, cmrt_get_graph_steps).  7: checkpoint
  * and restart (cmrt_save_bytes, cmrt_save, cmrt_load).  8: precision_reference
  * 0 is the node-mixture reference, the pure-colour one moved to 2.  9: the
- * 16-bit record carries reference dipoles and the rest populations (64 B/node). */
-#define CMRT_ABI_VERSION 9
+ * 16-bit record carries reference dipoles and the rest populations (64 B/node).
+ * 10: each 16-bit record carries its reference shape (a flag in D_0). */
+#define CMRT_ABI_VERSION 10
 
 typedef struct cmrt_ctx cmrt_ctx;     /* opaque, owned by the library */
 typedef struct cmrt_batch cmrt_batch; /* opaque, owned by the library */
@@ -106,7 +107,10 @@ typedef struct {
                                 equilibrium's velocity term and the recolour's segregation term
                                 (Eq. eq_re_color) per link direction; eight 16-bit pairs of
                                 deviations C_i - rho_C psi_i -/+ D_C of the moving links, FP16
-                                ones times 2^k with k = 14 for bulk densities up to 1);
+                                ones times 2^k with k = 14 for bulk densities up to 1; the
+                                lowest bit of D_0's red half selects the shape of psi: the
+                                equilibrium's, psi_d = psi_a / 4, or the one with ghost moment
+                                N = 0 that the step writes under ghost_N_mode 1);
                                 arithmetic is FP32 in all cases                                   */
     int32_t diag_every;      /* cmrt_step checks the non-finite flag every diag_every steps
                                 (synchronising the stream then); 0 = only at cmrt_diagnostics    */

@@ -92,7 +92,7 @@ _SIGNATURES = [
 CMRT_TUNE_FORCE = 1
 
 _lib = None
-ABI_VERSION = 9  # the layout of cmrt_params and the calls this binding was written for
+ABI_VERSION = 10  # the layout of cmrt_params and the calls this binding was written for
 
 
 def load(path: str = LIB_PATH):

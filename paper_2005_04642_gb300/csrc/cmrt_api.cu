@@ -262,7 +262,8 @@ StepParams derive(const cmrt_params& p) {
     // the kernels from the stored densities with psi_axis = mix_r rho_R +
     // mix_b rho_B over rho); reference 1: the lattice weights w_i; reference
     // 2: phi_i of the pure colour C (alpha_C).  Every reference has psi_axis a
-    // multiple of 2^-24 and psi_diag = psi_axis / 4, both exact in FP32.
+    // multiple of 2^-24; the kernels take psi_diag = psi_axis / 4 (exact in
+    // FP32) or, for records flagged N-free, the shape with ghost moment 0.
     s.mix_r = static_cast<float>((1.0 - p.alpha_r) / 5.0);
     s.mix_b = static_cast<float>((1.0 - p.alpha_b) / 5.0);
     // FP16 deviations are stored scaled by 2^k so that small ones stay in

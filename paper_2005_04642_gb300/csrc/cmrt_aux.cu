@@ -156,17 +156,32 @@ __global__ void k_unstream_in(const float* __restrict__ pre, int nx, int ny, int
 // (rho_C / rho) f_i along x and y (a state the step wrote gets its own S
 // back; any other state a valid one, whose rest the deviations carry).  The
 // rest populations are the remainder of rho_C after the moving links as the
-// step kernel decodes them, so that decoding conserves rho_C.  The axis reference weight (diagonal = axis
-// / 4) as a (red, blue) pair: the node's mixture (precision_reference 0; the
-// same rounding as the step kernel's) or per-colour constants.
-__device__ __forceinline__ float2 ref_weight_a(float rr, float rb, const StepParams& P) {
+// step kernel decodes them, so that decoding conserves rho_C.  The reference
+// weights of the axis and diagonal links as (red, blue) pairs, with the step
+// kernel's rounding (Layout16::weights): the node's mixture
+// (precision_reference 0) or per-colour constants; the diagonal weight a
+// quarter of the axis one (flag 0, the equilibrium's shape) or the rest
+// state with the same mass and energy and ghost moment N = 0 (flag 1).  The
+// flag is the lowest bit of D_0's red half; the encoder gives each record
+// the shape nearer to its own N.
+__device__ __forceinline__ void ref_weights(float rr, float rb, bool nfree, const StepParams& P, float2& wa,
+                                            float2& wd) {
+    float pr, pb;
     if (P.precision_reference == 0) {
         float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * __fdividef(1.0f, rr + rb);
         s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
-        const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);
-        return make_float2(pa, pa);
+        pr = pb = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);
+    } else {
+        pr = P.psi_r[1];
+        pb = P.psi_b[1];
     }
-    return make_float2(P.psi_r[1], P.psi_b[1]);
+    if (nfree) {
+        wa = make_float2(__fmaf_rn(pr, 0.5f, 1.0f / 18.0f), __fmaf_rn(pb, 0.5f, 1.0f / 18.0f));
+        wd = make_float2(__fmaf_rn(pr, 0.5f, -1.0f / 36.0f), __fmaf_rn(pb, 0.5f, -1.0f / 36.0f));
+    } else {
+        wa = make_float2(pr, pb);
+        wd = make_float2(__fmul_rn(pr, 0.25f), __fmul_rn(pb, 0.25f));
+    }
 }
 __device__ __forceinline__ unsigned pack2(float a, float b, int precision) {
     if (precision == kPrecF16) {
@@ -202,34 +217,42 @@ __global__ void k_encode(const float* __restrict__ post, StepParams P, char* __r
         const float a8 = fmaf(-kr, r[8] + b[8], r[8]), a4 = fmaf(-kr, r[4] + b[4], r[4]);
         const float a2 = fmaf(-kr, r[2] + b[2], r[2]), a6 = fmaf(-kr, r[6] + b[6], r[6]);
         unsigned* pairs = reinterpret_cast<unsigned*>(state + nodes * 16);
+        // the reference shape: the one whose ghost moment N (Dellar's weights
+        // 1, -2, 4 for the rest, axis and diagonal links) is nearer the record's
+        // (a shape's N per unit density: 1 - 12 (psi_a - psi_d); 0 for the N-free one)
+        float2 wa0, wd0;
+        ref_weights(rr, rb, false, P, wa0, wd0);
+        const float npl = rr * (1.0f - 12.0f * (wa0.x - wd0.x)) + rb * (1.0f - 12.0f * (wa0.y - wd0.y));
+        float N = r[0] + b[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) N = fmaf((i & 1) ? 4.0f : -2.0f, r[i] + b[i], N);
+        const bool nfree = fabsf(N) < fabsf(N - npl);
         float2 D[4];
         dipoles16(rr, rb, jx / rho, jy / rho, (a8 - a4) * (0.5f / lw(8)), (a2 - a6) * (0.5f / lw(2)), D);
         for (int j = 0; j < 4; ++j) {
-            const unsigned h = pack2(D[j].x, D[j].y, P.precision);
+            unsigned h = pack2(D[j].x, D[j].y, P.precision);
+            if (j == 0) h = (h & ~1u) | (nfree ? 1u : 0u);  // the flag
             pairs[j * nodes + n] = h;
             D[j] = unpack2(h, P.precision);  // the dipole as stored
         }
-        const float2 wa = ref_weight_a(rr, rb, P);
+        float2 wa, wd;
+        ref_weights(rr, rb, nfree, P, wa, wd);
         const float2 refa = make_float2(__fmul_rn(rr, wa.x), __fmul_rn(rb, wa.y));  // the decoder's
+        const float2 refd = make_float2(__fmul_rn(rr, wd.x), __fmul_rn(rb, wd.y));
         const float S = P.dev_scale;  // a power of two: the scaled deviation is the deviation, scaled exactly
         float sr = 0.f, sb = 0.f;     // the moving links as decoded, for the rest populations
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const float wr = (i & 1) ? 0.25f * wa.x : wa.x, wb = (i & 1) ? 0.25f * wa.y : wa.y;
+            const float wr = (i & 1) ? wd.x : wa.x, wb = (i & 1) ? wd.y : wa.y;
             const float2 Dj = D[dip_index(i)];
             const float sg = dip_neg(i) ? -1.0f : 1.0f;
             const float cr = r[i] - sg * Dj.x, cb = b[i] - sg * Dj.y;
             const unsigned h = pack2(fmaf(-rr * S, wr, cr * S), fmaf(-rb * S, wb, cb * S), P.precision);
             pairs[(3 + i) * nodes + n] = h;
             const float2 dd = unpack2(h, P.precision);
-            float xr, xb;
-            if (i & 1) {
-                xr = __fmaf_rn(refa.x, 0.25f, __fmul_rn(dd.x, P.dev_unscale));
-                xb = __fmaf_rn(refa.y, 0.25f, __fmul_rn(dd.y, P.dev_unscale));
-            } else {
-                xr = __fmaf_rn(dd.x, P.dev_unscale, refa.x);
-                xb = __fmaf_rn(dd.y, P.dev_unscale, refa.y);
-            }
+            const float2 ref = (i & 1) ? refd : refa;
+            float xr = __fmaf_rn(dd.x, P.dev_unscale, ref.x);
+            float xb = __fmaf_rn(dd.y, P.dev_unscale, ref.y);
             if (dip_neg(i)) {
                 xr = __fmaf_rn(Dj.x, -1.0f, xr);
                 xb = __fmaf_rn(Dj.y, -1.0f, xb);
@@ -253,23 +276,20 @@ __global__ void k_decode(const char* __restrict__ state, StepParams P, float* __
         const float2* own = reinterpret_cast<const float2*>(state) + n;
         const float2 rho = own[0], rest = own[nodes];
         const unsigned* pairs = reinterpret_cast<const unsigned*>(state + nodes * 16);
-        // the step kernel's decode: the axis reference pair rho psi_a (diagonal:
-        // over 4) plus the deviation, rounded once; then the dipole
-        const float2 wa = ref_weight_a(rho.x, rho.y, P);
+        // the step kernel's decode: the reference pair rho psi_i plus the
+        // deviation, rounded once; then the dipole
+        float2 wa, wd;
+        ref_weights(rho.x, rho.y, (pairs[n] & 1u) != 0, P, wa, wd);
         const float2 refa = make_float2(__fmul_rn(rho.x, wa.x), __fmul_rn(rho.y, wa.y));
+        const float2 refd = make_float2(__fmul_rn(rho.x, wd.x), __fmul_rn(rho.y, wd.y));
         post[n] = rest.x;
         post[9 * nodes + n] = rest.y;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const float2 d = unpack2(pairs[(3 + i) * nodes + n], P.precision);
-            float cr, cb;
-            if (i & 1) {
-                cr = __fmaf_rn(refa.x, 0.25f, __fmul_rn(d.x, P.dev_unscale));
-                cb = __fmaf_rn(refa.y, 0.25f, __fmul_rn(d.y, P.dev_unscale));
-            } else {
-                cr = __fmaf_rn(d.x, P.dev_unscale, refa.x);
-                cb = __fmaf_rn(d.y, P.dev_unscale, refa.y);
-            }
+            const float2 ref = (i & 1) ? refd : refa;
+            float cr = __fmaf_rn(d.x, P.dev_unscale, ref.x);
+            float cb = __fmaf_rn(d.y, P.dev_unscale, ref.y);
             const float2 D = unpack2(pairs[dip_index(i) * nodes + n], P.precision);
             if (dip_neg(i)) {
                 cr = __fmaf_rn(D.x, -1.0f, cr);

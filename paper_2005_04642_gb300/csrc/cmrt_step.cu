@@ -211,8 +211,9 @@ struct LayoutF32 {
 // (red, blue) pairs -- four reference dipoles D_0..D_3, then the deviations
 // d_i of the moving links i = 1..8 -- decoded as
 //   C_i = rho_C psi_i + (+/-) D_C,dip(i) + d_C,i / 2^k      (i >= 1)
-// (dip_index, dip_neg).  psi_i are the reference weights (axis psi_a,
-// diagonal psi_a / 4).  The step stores as dipoles (dipoles16) the
+// (dip_index, dip_neg).  psi_i are the reference weights of the axis and
+// diagonal links (weights()), of the shape that the lowest bit of D_0's red
+// half selects (the record's flag).  The step stores as dipoles (dipoles16) the
 // equilibrium's velocity term, with the node's post-collision velocity, and
 // the recolour's segregation term (Eq. eq_re_color), so that its deviations
 // are only the non-equilibrium and second-order parts of the populations:
@@ -225,18 +226,20 @@ struct LayoutF32 {
 //
 // A ring row keeps, per window column, the densities as copied --
 // overwritten by the thread that copied them, as soon as its copy has landed
-// (prep), with the axis reference pair (rho_R psi^R_a, rho_B psi^B_a) (the
-// diagonal one is it over 4, exactly) -- and the rest populations and the
-// twelve 16-bit pairs as copied.
+// (prep), with the axis reference pair (rho_R psi^R_a, rho_B psi^B_a) -- the
+// diagonal reference pair (prep), and the rest populations and the twelve
+// 16-bit pairs as copied.
 template <class H>
 struct Layout16 {
-    static constexpr int kRefBytes = kWin * 8;    // float2 per column: (rho_R, rho_B) -> axis reference pair
-    static constexpr int kRestBytes = kWin * 8;   // float2 per column: (R_0, B_0)
+    static constexpr int kRefBytes = 2 * kWin * 8;  // float2 per column: (rho_R, rho_B) -> axis pair; diagonal pair
+    static constexpr int kRestBytes = kWin * 8;     // float2 per column: (R_0, B_0)
     static constexpr int kPairBytes = kWin * 4;   // one 16-bit pair per column and plane
     static constexpr int kPairOff = kRefBytes + kRestBytes;
     static constexpr int kPairPlanes = 12;        // four dipoles, eight deviations
     static constexpr int kSlotBytes = kPairOff + kPairPlanes * kPairBytes;
-    static constexpr int kPairChunks = kPairPlanes * kPairBytes / 16;
+    // 16-byte chunks of the pair planes after D_0: each thread copies its own
+    // column of D_0, which carries the record's reference flag (prep)
+    static constexpr int kPairChunks = (kPairPlanes - 1) * kPairBytes / 16;
     static constexpr int kVecIters = (kPairChunks + kThreads - 1) / kThreads;
     static constexpr bool kPrep = true;
     static constexpr bool kCFront = true;  // stage C on the front warps (see chain_tile)
@@ -246,10 +249,10 @@ struct Layout16 {
     __device__ __forceinline__ static H from2(float a, float b);
     __device__ __forceinline__ static H from2x(float2 v) { return from2(v.x, v.y); }
 
-    // Each thread copies the densities and rest populations of its own window
-    // column (8 bytes each) and a share of the pair planes (16-byte chunks of
-    // four columns, or its own column's four bytes per plane when nx is not a
-    // multiple of 4).
+    // Each thread copies the densities, the rest populations and the dipole
+    // D_0 of its own window column (8, 8 and 4 bytes) and a share of the
+    // other pair planes (16-byte chunks of four columns, or its own column's
+    // four bytes per plane when nx is not a multiple of 4).
     template <bool VEC>
     struct Plan {
         static constexpr int kN = VEC ? kVecIters : kPairPlanes;
@@ -270,8 +273,8 @@ struct Layout16 {
 #pragma unroll
                 for (int m = 0; m < kN; ++m) {
                     const int c = threadIdx.x + m * kThreads;
-                    const int p = c / kPer;
-                    const int w4 = (c - p * kPer) * 4;
+                    const int p = 1 + c / kPer;
+                    const int w4 = (c - (p - 1) * kPer) * 4;
                     soff[m] = static_cast<unsigned>(kPairOff + p * kPairBytes + w4 * 4);
                     goff[m] = nodes * 16 + static_cast<size_t>(p) * nodes * 4 +
                               static_cast<size_t>(wrap(x0 - kHalo + w4, nx)) * 4;
@@ -291,6 +294,7 @@ struct Layout16 {
             const char* own = state + own_goff + row_nodes * 8;
             cp_async8(slot_addr + own_soff, own);
             cp_async8(slot_addr + kRefBytes + own_soff, own + rest_off);
+            if (VEC) cp_async4(slot_addr + kPairOff + own_soff / 2, state + 2 * rest_off + own_goff / 2 + row_nodes * 4);
 #pragma unroll
             for (int m = 0; m < kN; ++m) {
                 if (m < n) {
@@ -302,28 +306,50 @@ struct Layout16 {
         }
     };
 
-    // Axis reference weight psi_a of a node as a (red, blue) pair; psi_diag =
-    // psi_a / 4.  precision_reference 0: phi_i of Eq. eq_phi at the node's own
-    // mixture, psi_a = ((1 - alpha_R) rho_R + (1 - alpha_B) rho_B) / (5 rho)
-    // rounded to a multiple of 2^-24 (exact in FP32, as is psi_a / 4).  Other
-    // references: per-colour constants (psi_r, psi_b).
-    __device__ __forceinline__ static float2 weight_a(float rr, float rb, float inv_rho, const StepParams& P) {
+    // Reference weights (psi_a, psi_d) of a node's axis and diagonal links, as
+    // (red, blue) pairs.  psi_a: precision_reference 0 phi_i of Eq. eq_phi at
+    // the node's own mixture, ((1 - alpha_R) rho_R + (1 - alpha_B) rho_B) /
+    // (5 rho) rounded to a multiple of 2^-24; otherwise per-colour constants
+    // (psi_r, psi_b).  Two shapes, chosen per record by its flag (the lowest
+    // bit of D_0's red half): psi_d = psi_a / 4 (flag 0), the equilibrium's
+    // shape, whose ghost moment N is the equilibrium one; or (flag 1) the rest
+    // state with the same mass and energy and N = 0, which is what the
+    // collision leaves where N relaxes to 0 (ghost_N_mode 1): with Dellar's
+    // ghost weights g = (1, -2, 4) for the rest, axis and diagonal links,
+    // psi_a' = psi_a / 2 + 1/18 and psi_d' = psi_a / 2 - 1/36.  Any choice
+    // decodes correctly; a reference far from the populations only makes the
+    // deviations, and their 16-bit rounding, larger.
+    __device__ __forceinline__ static void weights(float rr, float rb, float inv_rho, bool nfree,
+                                                   const StepParams& P, float2& wa, float2& wd) {
+        float2 pa;
         if (P.precision_reference == 0) {
             float s5 = fmaf(P.mix_r, rr, P.mix_b * rb) * inv_rho;
             s5 = fminf(fmaxf(s5, 0.0f), 0.25f);
-            const float pa = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);  // a multiple of 2^-24
-            return make_float2(pa, pa);
+            const float q = __fsub_rn(__fadd_rn(s5, 0.5f), 0.5f);  // a multiple of 2^-24
+            pa = make_float2(q, q);
+        } else {
+            pa = make_float2(P.psi_r[1], P.psi_b[1]);
         }
-        return make_float2(P.psi_r[1], P.psi_b[1]);
+        if (nfree) {
+            wa = __ffma2_rn(pa, make_float2(0.5f, 0.5f), make_float2(1.0f / 18.0f, 1.0f / 18.0f));
+            wd = __ffma2_rn(pa, make_float2(0.5f, 0.5f), make_float2(-1.0f / 36.0f, -1.0f / 36.0f));
+        } else {
+            wa = pa;
+            wd = __fmul2_rn(pa, make_float2(0.25f, 0.25f));  // exact
+        }
     }
 
-    // Axis reference pair of window column t of a ring row whose copy has
-    // landed (the calling thread copied that column's densities itself, and
-    // only it reads or writes them).
+    // Reference pairs of window column t of a ring row whose copy has landed
+    // (the calling thread copied that column's densities and D_0 itself, and
+    // only it reads or writes the densities).
     __device__ __forceinline__ static void prep(char* slot, int t, const StepParams& P) {
         float2* ref = reinterpret_cast<float2*>(slot);
         const float2 rho = ref[t];
-        ref[t] = __fmul2_rn(rho, weight_a(rho.x, rho.y, rcp(rho.x + rho.y), P));
+        const unsigned d0 = reinterpret_cast<const unsigned*>(slot + kPairOff)[t];
+        float2 wa, wd;
+        weights(rho.x, rho.y, rcp(rho.x + rho.y), (d0 & 1u) != 0, P, wa, wd);
+        ref[t] = __fmul2_rn(rho, wa);
+        ref[kWin + t] = __fmul2_rn(rho, wd);
     }
 
     // link class of link i >= 1: axis (even i) or diagonal (odd i)
@@ -337,14 +363,12 @@ struct Layout16 {
             b = z.y;
             return;
         }
-        const float2 refa = reinterpret_cast<const float2*>(slot)[col];
+        const float2 ref = reinterpret_cast<const float2*>(slot)[(diag(i) ? kWin : 0) + col];
         const H* pairs = reinterpret_cast<const H*>(slot + kPairOff);
         const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale);
         const float2 d = to2(pairs[(3 + i) * kWin + col]);
         // reference pair plus the stored deviation times 2^-k (exact), rounded once
-        float2 c;
-        if (diag(i)) c = __ffma2_rn(refa, make_float2(0.25f, 0.25f), __fmul2_rn(d, un2));
-        else c = __ffma2_rn(d, un2, refa);
+        float2 c = __ffma2_rn(d, un2, ref);
         const float2 D = to2(pairs[dip_index(i) * kWin + col]);
         c = dip_neg(i) ? __ffma2_rn(D, make_float2(-1.0f, -1.0f), c) : __fadd2_rn(c, D);
         r = c.x;
@@ -363,22 +387,32 @@ struct Layout16 {
         H* pairs = reinterpret_cast<H*>(dst + nodes * 16) + node;
         float2 D[4];
         dipoles16(rr, rb, ux, uy, sx, sy, D);
+        // the reference flag: N-free shape where the collision relaxes N to 0
+        const bool nfree = P.ghost_N_mode == 1;
         float2 Dq[4];  // as stored, and as the decoder will use them
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const H h = from2x(D[j]);
+            H h = from2x(D[j]);
+            if (j == 0) {
+                // the flag replaces the lowest bit of D_0's red half: a reference
+                // value, so the change moves into the deviations exactly
+                unsigned u = *reinterpret_cast<const unsigned*>(&h);
+                u = (u & ~1u) | (nfree ? 1u : 0u);
+                h = *reinterpret_cast<const H*>(&u);
+            }
             pairs[j * nodes] = h;
             Dq[j] = to2(h);
         }
         float seg[9];
         segregation(sx * S, sy * S, seg);
         const float2 rho2 = make_float2(rr, rb);
-        const float2 wa = weight_a(rr, rb, inv_rho, P);
-        const float2 wd = __fmul2_rn(wa, make_float2(0.25f, 0.25f));  // exact
-        const float2 refa = __fmul2_rn(rho2, wa);                     // the decoder's axis reference pair
+        float2 wa, wd;
+        weights(rr, rb, inv_rho, nfree, P, wa, wd);
+        const float2 refa = __fmul2_rn(rho2, wa);  // the decoder's reference pairs
+        const float2 refd = __fmul2_rn(rho2, wd);
         const float2 a2 = make_float2(rr * inv_rho * S, rb * inv_rho * S), mrho = make_float2(-rr * S, -rb * S);
         const float2 mS = make_float2(-S, -S), pS = make_float2(S, S), m1 = make_float2(-1.0f, -1.0f);
-        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale), q2 = make_float2(0.25f, 0.25f);
+        const float2 un2 = make_float2(P.dev_unscale, P.dev_unscale);
         // The rest populations are what is left of rho_R and rho_B after the
         // moving links as the decoder will see them (pair(), bit for bit), so
         // that every record decodes to exactly its colour densities: colour mass
@@ -392,7 +426,7 @@ struct Layout16 {
             const H h = from2x(__ffma2_rn(mrho, diag(i) ? wd : wa, C));
             pairs[(3 + i) * nodes] = h;
             const float2 d = to2(h);
-            float2 c = diag(i) ? __ffma2_rn(refa, q2, __fmul2_rn(d, un2)) : __ffma2_rn(d, un2, refa);
+            float2 c = __ffma2_rn(d, un2, diag(i) ? refd : refa);
             c = dip_neg(i) ? __ffma2_rn(Dj, m1, c) : __fadd2_rn(c, Dj);
             sum = __fadd2_rn(sum, c);
         }

@@ -206,17 +206,19 @@ def ba_channel(H=200, nx=4, nu=0.333, G=1e-8, width=2.0, beta=0.67, stencil_orde
 MICRO_CURRENT_LAMBDAS = (0.001, 0.01, 0.1, 10.0, 100.0, 1000.0)
 
 
-def micro_current_drop(Lambda, n=200, radius=60.0, fixed_K=False, sigma=0.005, beta=0.67, nu=1.0 / 6.0):
+def micro_current_drop(Lambda, n=200, radius=60.0, fixed_K=False, sigma=0.005, beta=0.67, nu=1.0 / 6.0,
+                       centre=None):
     """Static red drop of Sec. 4.2 (the micro-current study): radius 60,
     centred in a 200 x 200 periodic box, at rest.  Lambda = rho0_R / rho0_B
     with the larger density 1; alpha as in the paper's tables (the lighter
     fluid 0.5).  fixed_K replaces the computed curvature by K = 1/R.  The
     paper prints neither sigma, beta nor nu for this study: 0.005, 0.67 and
-    1/6 as in the static-drop workload."""
+    1/6 as in the static-drop workload.  centre (x, y) moves the drop off
+    the box centre (default (n/2, n/2), a lattice node)."""
     rho0_r, rho0_b = (1.0, 1.0 / Lambda) if Lambda >= 1.0 else (Lambda, 1.0)
     p = base_params(n, n, rho0_r=rho0_r, rho0_b=rho0_b, sigma=sigma, beta=beta,
                     lambda3_r=lambda3_for_nu(nu), lambda3_b=lambda3_for_nu(nu))
     if fixed_K:
         p["curvature_mode"], p["fixed_K"] = 1, 1.0 / radius
-    rho_n = drops_field(n, n, [(n / 2.0, n / 2.0)], [radius])
+    rho_n = drops_field(n, n, [(n / 2.0, n / 2.0) if centre is None else tuple(centre)], [radius])
     return p, rho_n, np.zeros((2, n, n))

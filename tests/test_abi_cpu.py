@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(cm):
 
 
 def test_abi_version_and_struct_size(cm):
-    assert cm.cmrt_abi_version() == 9
+    assert cm.cmrt_abi_version() == 10
     assert cm.load().cmrt_params_size() == ctypes.sizeof(cm.cmrt_params)
 
 

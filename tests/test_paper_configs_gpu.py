@@ -128,12 +128,18 @@ def test_ba_channel_steady_state_against_app_d():
     assert out[6]["asymmetry"] <= 1e-3
 
 
-@pytest.mark.parametrize("Lam", [0.001, 1000.0])
+@pytest.mark.parametrize("Lam", I.MICRO_CURRENT_LAMBDAS)
 @pytest.mark.parametrize("fixed", [False, True], ids=["computed_K", "fixed_K"])
 def test_micro_current_replica_matches_oracle(Lam, fixed):
     """64 x 64 replica of the micro-current drop (radius 0.3 of the box, as
-    60 / 200), 100 steps, at the extreme density ratios of the tables."""
-    d, rn, u = I.micro_current_drop(Lam, n=64, radius=19.2, fixed_K=fixed)
+    60 / 200), 100 steps, at every density ratio of the tables.  The centre
+    sits off the lattice nodes: at a drop centred on a node the colour
+    gradient there is zero in exact arithmetic, so the FP64 oracle leaves n
+    at 0 (below the threshold of the unit normal) while FP32 rounding leaves
+    a gradient of a few ulps whose direction is noise, and the two runs part
+    at that node by more than rounding (u 9.4e-5 at Lambda = 100 against
+    6.8e-6 off the node)."""
+    d, rn, u = I.micro_current_drop(Lam, n=64, radius=19.2, fixed_K=fixed, centre=(32.3, 31.8))
     _parity(d, rn, u)
 
 
