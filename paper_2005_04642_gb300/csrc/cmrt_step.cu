@@ -330,13 +330,12 @@ struct Layout16 {
         } else {
             pa = make_float2(P.psi_r[1], P.psi_b[1]);
         }
-        if (nfree) {
-            wa = __ffma2_rn(pa, make_float2(0.5f, 0.5f), make_float2(1.0f / 18.0f, 1.0f / 18.0f));
-            wd = __ffma2_rn(pa, make_float2(0.5f, 0.5f), make_float2(-1.0f / 36.0f, -1.0f / 36.0f));
-        } else {
-            wa = pa;
-            wd = __fmul2_rn(pa, make_float2(0.25f, 0.25f));  // exact
-        }
+        // one form for both shapes: pa * s + c, with (s, c) = (1, 0) and (1/4, 0)
+        // exact for the equilibrium's
+        const float sa = nfree ? 0.5f : 1.0f, ca = nfree ? 1.0f / 18.0f : 0.0f;
+        const float sd = nfree ? 0.5f : 0.25f, cd = nfree ? -1.0f / 36.0f : 0.0f;
+        wa = __ffma2_rn(pa, make_float2(sa, sa), make_float2(ca, ca));
+        wd = __ffma2_rn(pa, make_float2(sd, sd), make_float2(cd, cd));
     }
 
     // Reference pairs of window column t of a ring row whose copy has landed
