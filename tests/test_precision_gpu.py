@@ -295,6 +295,52 @@ def test_buoyant_replica_512_10k_steps():
             assert table[name][k] <= 1e-3, (name, k, table[name][k])
 
 
+@pytest.mark.parametrize("prec", [FP16, BF16])
+def test_full_size_drops_workload_sampled_nodes(prec):
+    """The 8192^2 periodic drops workload with 16-bit storage, in the
+    benchmark's launch configuration: one step from the decoded state,
+    checked at sampled nodes against the oracle stepping a 13 x 13 window
+    around each (a node depends on nothing beyond radius 5 in one step).
+    The two differ by the record's rounding of the new post-collision
+    populations: the bar is twice what _record16 gives at the same node,
+    plus the FP32 path's 2e-6; colour mass is conserved over 20 steps."""
+    d, rn, u = I.drops_8192()
+    lat = cm.Lattice(dict(d, precision=prec), rn, u)
+    lat.step(3)
+    pre = lat.populations()
+    rng = np.random.default_rng(0)
+    inter = np.argwhere(np.abs(rn) < 0.9)
+    picks = [tuple(inter[i]) for i in rng.choice(len(inter), 24, replace=False)]
+    picks += [tuple(x) for x in rng.integers(0, 8192, size=(8, 2))]
+    picks += [(0, 0), (8191, 8191), (0, 8191), (4095, 8190)]
+    h = 6
+    wins = []
+    for (y, x) in picks:
+        ys = torch.arange(y - h, y + h + 1, device="cuda") % 8192
+        xs = torch.arange(x - h, x + h + 1, device="cuda") % 8192
+        wins.append(pre[:, :, ys][:, :, :, xs].double().cpu().numpy())
+    del pre
+    m0 = lat.diagnostics()
+    lat.step(1)
+    post = lat.populations()
+    got = [post[:, :, y, x].double().cpu().numpy() for (y, x) in picks]
+    del post
+    lat.step(19)
+    m1 = lat.diagnostics()
+    lat.close()
+    pw = _oracle_params(dict(d, nx=2 * h + 1, ny=2 * h + 1))
+    for w, g in zip(wins, got):
+        Rpp, Bpp = O.collide_and_recolour(w[0], w[1], pw)
+        ref = np.stack([O.stream(Rpp, pw)[:, h, h], O.stream(Bpp, pw)[:, h, h]])
+        Rq, Bq = _record16(Rpp, Bpp, pw, prec, pw.ghost_N_mode == 1)
+        mod = np.stack([O.stream(Rq, pw)[:, h, h], O.stream(Bq, pw)[:, h, h]])
+        scale = max(np.abs(ref).max(), 0.1)
+        assert np.abs(g - ref).max() <= 2.0 * np.abs(mod - ref).max() + 2e-6 * scale, \
+            (np.abs(g - ref).max(), np.abs(mod - ref).max())
+    assert abs(m1["mass_r"] - m0["mass_r"]) / m0["mass_r"] <= 1e-6
+    assert abs(m1["mass_b"] - m0["mass_b"]) / m0["mass_b"] <= 1e-6
+
+
 def test_fp16_close_to_fp32_on_full_size_field():
     """The reduced-precision form tracks the (oracle-checked) FP32 path on the
     16384 x 8192 buoyant field over 50 steps, within the FP16 bar."""
