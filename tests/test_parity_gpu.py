@@ -210,8 +210,10 @@ def test_layered_full_width_10k_steps_parity_bar(visc_ratio):
     oracle whose state is rounded to FP32 after every step drifts by
     2.2e-6 (red) and 3.6e-6 to 4.4e-6 (blue) over these 10k steps, because
     the light colour's populations sit near 1e-3 and every column makes the
-    same rounding errors -- so the bar is 5e-6 here, not the 1e-6 that the
-    static drop meets."""
+    same rounding errors.  The step measures 1.2e-6 (red) and 3.6e-7 (blue)
+    at viscosity ratio 1 and 8.6e-7 and 7.6e-7 at ratio 10, below that floor
+    but not always below the 1e-6 that the static drop meets, so the bar is
+    2e-6 here."""
     d, rn, u = I.layered_channel(nx=1024, ny=128, Lambda=100.0, visc_ratio=visc_ratio, g=1e-6)
     ds, rns, us = I.layered_channel(nx=4, ny=128, Lambda=100.0, visc_ratio=visc_ratio, g=1e-6)
     p, R, B = _oracle_run(ds, rns, us, 10000)
@@ -229,8 +231,8 @@ def test_layered_full_width_10k_steps_parity_bar(visc_ratio):
         scale = uref if k in ("ux", "uy") else np.abs(ref).max()
         err = np.abs(g[k] - ref).max() / scale
         assert err <= 1e-3, (k, err)
-    assert abs(d1["mass_r"] - d0["mass_r"]) / d0["mass_r"] <= 5e-6
-    assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 5e-6
+    assert abs(d1["mass_r"] - d0["mass_r"]) / d0["mass_r"] <= 2e-6
+    assert abs(d1["mass_b"] - d0["mass_b"]) / d0["mass_b"] <= 2e-6
 
 
 def test_diagnostics_match_oracle():
