@@ -77,13 +77,19 @@ CASES = [
     ("fixedK_ghostN", 36, 44, False, {"curvature_mode": 1, "fixed_K": 0.05, "ghost_N_mode": 1}),
     ("rates_force", 64, 24, False, {"lambda3_r": 1.6, "lambda3_b": 0.7, "lambda6": 1.3, "lambda7": 0.6,
                                     "g_vol": (1e-5, 2e-5), "sigma": 0.02}),
+    # degenerate parameters: no segregation and no interfacial tension (the
+    # recolour only splits f+ by the colour fractions, G only the body force)
+    ("beta0_sigma0", 40, 32, True, {"beta": 0.0, "sigma": 0.0, "g_acc": (1e-5, 0.0)}),
+    # the tables' extreme density ratios, either colour the lighter
+    ("lambda1000", 48, 36, False, {"rho0_b": 0.001}),
+    ("lambda0.001", 36, 48, True, {"rho0_r": 0.001, "rho0_b": 1.0}),
 ]
 
 
 @pytest.mark.parametrize("name,nx,ny,wall,extra", CASES, ids=[c[0] for c in CASES])
 def test_steps_match_oracle_elementwise(name, nx, ny, wall, extra):
     rn, u = I.random_state_fields(nx, ny, seed=zlib.crc32(name.encode()) % 1000)
-    d = I.base_params(nx, ny, rho0_r=1.0, rho0_b=0.1, wall_y=wall, **extra)
+    d = I.base_params(nx, ny, **dict(dict(rho0_r=1.0, rho0_b=0.1, wall_y=wall), **extra))
     nsteps = 3
     p, R, B = _oracle_run(d, rn, u, nsteps)
     lat = cm.Lattice(d, rn, u)
